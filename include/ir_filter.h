@@ -1,0 +1,154 @@
+/*
+ * ir_filter.h - C ABI of the GB300 FNR impulse filter for infrared frames.
+ *
+ * The filter is the "fast noise reduction" (FNR) method of arXiv 1201.3972:
+ *   - S_xy is the k x k window around pixel p(x, y), centre included (Sec. 3.3);
+ *   - g_max = max S_xy, g_min = min S_xy (Eq. 3a, 3b);
+ *   - p(x, y) is noisy iff g(x, y) == g_min or g(x, y) == g_max (Sec. 3.3,
+ *     step 2) - there is no threshold or other preset parameter;
+ *   - a noisy pixel is replaced by the median g_m of S_xy and every other
+ *     pixel is left unchanged (Sec. 3.4).
+ * Readings this library fixes where the paper is silent: the border is
+ * replicated (every pixel gets a full k x k window), every window reads the
+ * unfiltered input (one non-recursive pass), ties with g_min/g_max flag, and
+ * k is odd so g_m is the element of rank (k*k-1)/2 of the sorted window.
+ * Results are integer-exact: every entry point returns the same bytes as a
+ * plain CPU evaluation of the rules above.
+ *
+ * Memory: every frame pointer is a CUDA DEVICE pointer to a row-pitched
+ * image (pitch in bytes, rows contiguous). The caller owns all frame memory.
+ * A handle owns its scratch memory (grown on demand), cached tensor maps,
+ * its tuning table and a device status word. Handles are not thread-safe:
+ * use one per host thread (several may share a device).
+ *
+ * Streams: `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream). Calls are asynchronous: argument errors are returned at
+ * once, launch errors are returned by the call, and results (and device-side
+ * errors) are valid after the stream is synchronised.
+ *
+ * Errors never abort the process: every entry point returns an ir_status and
+ * ir_filter_last_error() gives a one-line description of the last failure.
+ */
+#ifndef IR_FILTER_H
+#define IR_FILTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IR_OK = 0,
+  IR_EINVAL = 1,        /* bad argument (k even/out of range, H or W < 1, NULL, pitch too small, overlap) */
+  IR_EALIGN = 2,        /* reserved: alignment is never an error (unaligned frames take a plain-load path) */
+  IR_ENOMEM = 3,        /* device scratch could not be grown / admission refused for lack of memory */
+  IR_ECUDA = 4,         /* a CUDA runtime call failed (see ir_filter_last_error) */
+  IR_ETIMEOUT = 5,      /* a bounded device-side wait gave up (reported by ir_filter_sync_status) */
+  IR_EBUSY = 6,         /* no free slot right now (server admission) */
+  IR_EUNSUPPORTED = 7   /* configuration not built into this library */
+} ir_status;
+
+/* Pixel types. IR_U14 is 16-bit storage whose values the caller promises are
+ * <= 16383 (14-bit sensors); the result is exact for any 16-bit value anyway. */
+typedef enum { IR_U8 = 0, IR_U16 = 1, IR_U14 = 2 } ir_dtype;
+
+/* Median-selection strategies (all give identical results; they differ in speed). */
+typedef enum {
+  IR_ALGO_AUTO = 0,          /* tuned choice for (dtype, k) */
+  IR_ALGO_DENSE3 = 1,        /* k = 3 only: median for every pixel with shared column sorts, packed 16x2 */
+  IR_ALGO_NETWORK = 2,       /* k <= 9: flagged pixels compacted, register selection network each */
+  IR_ALGO_BITPLANE = 3       /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
+} ir_algo;
+
+/* Kernel configuration for one (dtype, k) class. tile_w, tile_h: output tile
+ * in pixels (multiples of 8; tile_w + halo <= 256 pixels). ctas_per_sm: 0 = as
+ * many as fit. */
+typedef struct {
+  int tile_w;
+  int tile_h;
+  int algo;          /* ir_algo */
+  int ctas_per_sm;
+} ir_kernel_config;
+
+typedef struct ir_filter ir_filter;
+
+/* Create a handle on CUDA device `device` (made current for the call; the
+ * calling thread's current device is restored afterwards). *out is NULL on
+ * failure. Largest supported window: 21. */
+ir_status ir_filter_create(ir_filter **out, int device);
+
+/* Destroy a handle and free everything it owns (NULL-safe). Pending work on
+ * streams that used it must be complete. */
+void ir_filter_destroy(ir_filter *h);
+
+/* Filter one frame IN PLACE (the input is first copied into handle scratch,
+ * then filtered back into `frame`). H, W >= 1; pitch >= W * bytes per pixel;
+ * k odd in [3, 21] (k may exceed H or W: the border is replicated).
+ * Uses scratch memory of H * W * bytes-per-pixel. */
+ir_status ir_filter_run(ir_filter *h, void *frame, int H, int W, size_t pitch_bytes,
+                        ir_dtype dtype, int k, void *cuda_stream);
+
+/* Filter one frame out of place. `in` and `out` must not overlap. If
+ * `flagged_count` is not NULL it must be a DEVICE pointer; it is set to the
+ * number of noisy pixels (the number of medians taken, Table 1's "sort
+ * times"). No scratch memory is used. */
+ir_status ir_filter_run2(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch,
+                         int H, int W, ir_dtype dtype, int k, void *cuda_stream,
+                         unsigned long long *flagged_count);
+
+/* One frame of a batch: same meaning as the arguments of ir_filter_run2. */
+typedef struct {
+  const void *in;
+  void *out;
+  int H, W;
+  size_t in_pitch, out_pitch;
+  ir_dtype dtype;
+  int k;
+  unsigned long long *flagged_count;  /* nullable, device pointer */
+} ir_frame_desc;
+
+/* Filter n frames of mixed sizes, dtypes and windows in one CUDA-graph launch:
+ * one persistent kernel per (dtype, k) class present, the classes running
+ * concurrently as branches of the graph. The graph is built on first use of
+ * a descriptor set and replayed while the same set (same pointers, shapes,
+ * windows) is submitted again. Outputs must not overlap any input. */
+ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, void *cuda_stream);
+
+/* Explicit batch plans: validate and upload a descriptor set once, capture
+ * its graph, then launch it any number of times. */
+typedef struct ir_batch_plan ir_batch_plan;
+ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, ir_batch_plan **out);
+ir_status ir_batch_plan_launch(ir_batch_plan *plan, void *cuda_stream);
+/* Number of kernel launches one replay of the plan performs. */
+int ir_batch_plan_kernel_count(const ir_batch_plan *plan);
+void ir_batch_plan_destroy(ir_batch_plan *plan);
+
+/* Read and clear the handle's device status word (synchronises the device).
+ * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call. */
+ir_status ir_filter_sync_status(ir_filter *h);
+
+/* Tuning. ir_filter_autotune times every built candidate for (dtype, k) on a
+ * synthetic H x W frame on `cuda_stream` and keeps the fastest; the table is
+ * per handle. get/set read or override one entry. */
+ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, void *cuda_stream);
+ir_status ir_filter_get_config(ir_filter *h, ir_dtype dtype, int k, ir_kernel_config *out);
+ir_status ir_filter_set_config(ir_filter *h, ir_dtype dtype, int k, const ir_kernel_config *cfg);
+
+/* Number of FNR kernel launches this handle has issued (graph replays count
+ * each kernel node). */
+unsigned long long ir_filter_launch_count(const ir_filter *h);
+
+const char *ir_status_string(ir_status s);
+/* Last error message of this handle ("" if none). NULL handle: last global error. */
+const char *ir_filter_last_error(const ir_filter *h);
+
+/* Library version, e.g. "0.1.0". */
+const char *ir_filter_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IR_FILTER_H */

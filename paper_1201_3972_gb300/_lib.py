@@ -1,0 +1,269 @@
+"""ctypes binding of libirfnr.so (the C ABI in include/ir_filter.h).
+
+Every ``ir_*`` function here has the name and argument order of its C
+counterpart; this module only converts arguments (torch tensors or integer
+device addresses, streams) and turns non-OK statuses into exceptions. All
+filtering happens in the library's CUDA kernels. If the library cannot be
+loaded the first call raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libirfnr.so")
+
+IR_OK, IR_EINVAL, IR_EALIGN, IR_ENOMEM, IR_ECUDA, IR_ETIMEOUT, IR_EBUSY, IR_EUNSUPPORTED = range(8)
+IR_U8, IR_U16, IR_U14 = 0, 1, 2
+IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE = 0, 1, 2, 3
+ALGO_NAMES = {IR_ALGO_AUTO: "auto", IR_ALGO_DENSE3: "dense3", IR_ALGO_NETWORK: "network",
+              IR_ALGO_BITPLANE: "bitplane"}
+
+EXPORTED = (
+    "ir_filter_create", "ir_filter_destroy", "ir_filter_run", "ir_filter_run2", "ir_filter_run_batch",
+    "ir_batch_plan_create", "ir_batch_plan_launch", "ir_batch_plan_kernel_count", "ir_batch_plan_destroy",
+    "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
+    "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
+)
+
+
+class IrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class ir_kernel_config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int), ("algo", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int)]
+
+
+class ir_frame_desc(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("in_pitch", ctypes.c_size_t), ("out_pitch", ctypes.c_size_t), ("dtype", ctypes.c_int),
+                ("k", ctypes.c_int), ("flagged_count", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(path: Optional[str] = None):
+    """Load libirfnr.so (built by ``__graft_entry__.build()`` or ``_build.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is not built; run paper_1201_3972_gb300._build.build()")
+        lib = ctypes.CDLL(p)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "ir_filter_create": ([ctypes.POINTER(vp), i32], i32),
+            "ir_filter_destroy": ([vp], None),
+            "ir_filter_run": ([vp, vp, i32, i32, sz, i32, i32, vp], i32),
+            "ir_filter_run2": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
+            "ir_filter_run_batch": ([vp, ctypes.POINTER(ir_frame_desc), i32, vp], i32),
+            "ir_batch_plan_create": ([vp, ctypes.POINTER(ir_frame_desc), i32, ctypes.POINTER(vp)], i32),
+            "ir_batch_plan_launch": ([vp, vp], i32),
+            "ir_batch_plan_kernel_count": ([vp], i32),
+            "ir_batch_plan_destroy": ([vp], None),
+            "ir_filter_sync_status": ([vp], i32),
+            "ir_filter_autotune": ([vp, i32, i32, i32, i32, vp], i32),
+            "ir_filter_get_config": ([vp, i32, i32, ctypes.POINTER(ir_kernel_config)], i32),
+            "ir_filter_set_config": ([vp, i32, i32, ctypes.POINTER(ir_kernel_config)], i32),
+            "ir_filter_launch_count": ([vp], ctypes.c_ulonglong),
+            "ir_status_string": ([i32], ctypes.c_char_p),
+            "ir_filter_last_error": ([vp], ctypes.c_char_p),
+            "ir_filter_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(lib, h, status: int) -> None:
+    if status != IR_OK:
+        msg = lib.ir_filter_last_error(h)
+        raise IrError(status, (msg or b"").decode() or lib.ir_status_string(status).decode())
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor, or an integer address as is."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def dtype_code(t, u14: bool = False) -> int:
+    import torch
+    if t.dtype == torch.uint8:
+        return IR_U8
+    if t.dtype in (torch.uint16, torch.int16):
+        return IR_U14 if u14 else IR_U16
+    raise TypeError(f"unsupported tensor dtype {t.dtype}: use uint8 or uint16")
+
+
+def _frame_geometry(t):
+    """(H, W, pitch_bytes) of a 2-D tensor with contiguous rows."""
+    if t.dim() != 2:
+        raise ValueError("frames are 2-D (H, W) tensors")
+    if t.stride(1) != 1:
+        raise ValueError("frame rows must be contiguous")
+    H, W = t.shape
+    pitch = t.stride(0) * t.element_size() if H > 1 else W * t.element_size()
+    return int(H), int(W), int(pitch)
+
+
+class Filter:
+    """One library handle (``ir_filter``) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.ir_filter_create(ctypes.byref(h), int(device))
+        _check(self.lib, None, st)
+        self.h = h
+        self.device = device
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.ir_filter_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- single frames ------------------------------------------------------
+    def ir_filter_run(self, frame, H: int, W: int, pitch: int, dtype: int, k: int, stream=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_run(self.h, _ptr(frame), H, W, pitch, dtype, k, _stream(stream)))
+
+    def ir_filter_run2(self, src, in_pitch: int, dst, out_pitch: int, H: int, W: int, dtype: int, k: int,
+                       stream=None, flagged_count=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_run2(self.h, _ptr(src), in_pitch, _ptr(dst), out_pitch, H, W,
+                                                         dtype, k, _stream(stream), _ptr(flagged_count) or None))
+
+    def run(self, frame, k: int, u14: bool = False, stream=None) -> None:
+        """In-place filter of a 2-D uint8/uint16 CUDA tensor."""
+        H, W, pitch = _frame_geometry(frame)
+        self.ir_filter_run(frame, H, W, pitch, dtype_code(frame, u14), k, stream)
+
+    def run2(self, src, dst, k: int, u14: bool = False, stream=None, flagged_count=None) -> None:
+        """Out-of-place filter; ``flagged_count`` is an optional 1-element int64 CUDA tensor."""
+        H, W, ip = _frame_geometry(src)
+        H2, W2, op = _frame_geometry(dst)
+        if (H, W) != (H2, W2) or src.dtype != dst.dtype:
+            raise ValueError("src and dst must have the same shape and dtype")
+        self.ir_filter_run2(src, ip, dst, op, H, W, dtype_code(src, u14), k, stream, flagged_count)
+
+    # -- batches --------------------------------------------------------------
+    @staticmethod
+    def make_descs(frames):
+        """frames: iterable of dicts with keys in, out, k and optional u14, flagged."""
+        frames = list(frames)
+        arr = (ir_frame_desc * len(frames))()
+        for i, f in enumerate(frames):
+            H, W, ip = _frame_geometry(f["in"])
+            _, _, op = _frame_geometry(f["out"])
+            arr[i].in_ = _ptr(f["in"])
+            arr[i].out = _ptr(f["out"])
+            arr[i].H, arr[i].W = H, W
+            arr[i].in_pitch, arr[i].out_pitch = ip, op
+            arr[i].dtype = dtype_code(f["in"], f.get("u14", False))
+            arr[i].k = int(f["k"])
+            arr[i].flagged_count = _ptr(f.get("flagged")) or None
+        return arr
+
+    def ir_filter_run_batch(self, descs, n: int, stream=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_run_batch(self.h, descs, n, _stream(stream)))
+
+    def run_batch(self, frames, stream=None) -> None:
+        descs = self.make_descs(frames)
+        self.ir_filter_run_batch(descs, len(descs), stream)
+
+    def plan(self, frames) -> "BatchPlan":
+        descs = self.make_descs(frames)
+        return BatchPlan(self, descs)
+
+    # -- status, tuning ---------------------------------------------------------
+    def ir_filter_sync_status(self) -> int:
+        return self.lib.ir_filter_sync_status(self.h)
+
+    def sync_status(self) -> None:
+        _check(self.lib, self.h, self.ir_filter_sync_status())
+
+    def launch_count(self) -> int:
+        return int(self.lib.ir_filter_launch_count(self.h))
+
+    def autotune(self, dtype: int, k: int, H: int, W: int, stream=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_autotune(self.h, dtype, k, H, W, _stream(stream)))
+
+    def get_config(self, dtype: int, k: int) -> dict:
+        c = ir_kernel_config()
+        _check(self.lib, self.h, self.lib.ir_filter_get_config(self.h, dtype, k, ctypes.byref(c)))
+        return {"tile_w": c.tile_w, "tile_h": c.tile_h, "algo": c.algo, "ctas_per_sm": c.ctas_per_sm}
+
+    def set_config(self, dtype: int, k: int, tile_w: int, tile_h: int, algo: int, ctas_per_sm: int = 0) -> None:
+        c = ir_kernel_config(tile_w, tile_h, algo, ctas_per_sm)
+        _check(self.lib, self.h, self.lib.ir_filter_set_config(self.h, dtype, k, ctypes.byref(c)))
+
+
+class BatchPlan:
+    """An uploaded descriptor set with its captured graph (``ir_batch_plan``)."""
+
+    def __init__(self, flt: Filter, descs):
+        self.flt = flt
+        self.lib = flt.lib
+        self.descs = descs
+        p = ctypes.c_void_p()
+        _check(self.lib, flt.h, self.lib.ir_batch_plan_create(flt.h, descs, len(descs), ctypes.byref(p)))
+        self.p = p
+
+    @property
+    def kernel_count(self) -> int:
+        return int(self.lib.ir_batch_plan_kernel_count(self.p))
+
+    def launch(self, stream=None) -> None:
+        _check(self.lib, self.flt.h, self.lib.ir_batch_plan_launch(self.p, _stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "p", None):
+            self.lib.ir_batch_plan_destroy(self.p)
+            self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,100 @@
+// Kernel parameter blocks and shared-memory layout, shared by the host code
+// and the kernels of the FNR filter library.
+#pragma once
+
+#include <cuda.h>
+#include <cstdint>
+
+namespace fnr {
+
+constexpr int kThreads = 256;          // threads per CTA for every kernel
+constexpr int kMaxK = 21;              // largest window built
+constexpr int kNumK = (kMaxK - 3) / 2 + 1;
+
+enum Algo : int { ALGO_AUTO = 0, ALGO_DENSE3 = 1, ALGO_NETWORK = 2, ALGO_BITPLANE = 3 };
+
+// Frame flags
+constexpr int kFrameTmaIn = 1;     // load tiles with TMA (16 B aligned base and pitch)
+constexpr int kFrameTmaOut = 2;    // store tiles with TMA
+
+// One frame as the kernel sees it. The tensor maps come first: they need
+// 128-byte alignment.
+struct alignas(128) FrameDev {
+  CUtensorMap tin;                 // box = (tile_w + 2*xoff) x (tile_h + 2r), u8/u16
+  CUtensorMap tout;                // box = tile_w x tile_h
+  const unsigned char *in;
+  unsigned char *out;
+  long long in_pitch;
+  long long out_pitch;
+  int H, W;
+  int tiles_x, tiles_y;
+  int tile_begin;                  // first global tile index of this frame in its class
+  int flags;
+  unsigned long long *flagged;     // nullable, device
+};
+
+struct alignas(128) FnrParams {
+  FrameDev single;                 // used when table == nullptr
+  const FrameDev *table;           // device array of nframes frames (batch)
+  int nframes;
+  int total_tiles;
+  int tile_w, tile_h;
+  unsigned int *status;            // device status word (bit 0: bounded wait timed out)
+  unsigned long long *launches;    // device launch counter (nullable)
+};
+
+constexpr unsigned int kStatusTimeout = 1u;
+
+__host__ __device__ constexpr int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Left halo (in pixels) rounded up so that every TMA box starts on a 16-byte
+// boundary: x0 - xoff is a multiple of 16 / esize when x0 is.
+__host__ __device__ constexpr int xoff_for(int r, int esize) {
+  return align_up(r, 16 / esize);
+}
+
+// Shared-memory layout of one CTA (byte offsets). Identical on host and device.
+struct Layout {
+  int r, bw, bh, vw, pw, nbmax;
+  int off_stage[2];
+  int off_out[2];
+  int off_list;
+  int off_vmin, off_vmax;
+  int off_planes;
+  int off_bar;
+  int off_misc;
+  int total;
+};
+
+__host__ __device__ inline Layout make_layout(int esize, int k, int algo, int tile_h, int tile_w) {
+  Layout L{};
+  L.r = (k - 1) / 2;
+  const int xoff = xoff_for(L.r, esize);
+  L.bw = tile_w + 2 * xoff;
+  L.bh = tile_h + 2 * L.r;
+  L.vw = tile_w + 2 * L.r;
+  L.pw = (L.bw + 31) / 32 + 1;
+  L.nbmax = 8 * esize;
+  int off = 0;
+  const int stage = align_up(L.bw * L.bh * esize, 128);
+  const int outb = align_up(tile_w * tile_h * esize, 128);
+  L.off_stage[0] = off; off += stage;
+  L.off_stage[1] = off; off += stage;
+  L.off_out[0] = off; off += outb;
+  L.off_out[1] = off; off += outb;
+  L.off_list = L.off_vmin = L.off_vmax = L.off_planes = -1;
+  if (algo != ALGO_DENSE3) {
+    L.off_list = off; off += align_up(tile_w * tile_h * 2, 128);
+    L.off_vmin = off; off += align_up(tile_h * L.vw * 2, 128);
+    L.off_vmax = off; off += align_up(tile_h * L.vw * 2, 128);
+  }
+  if (algo == ALGO_BITPLANE) {
+    L.off_planes = off; off += align_up(L.nbmax * L.bh * L.pw * 4, 128);
+  }
+  L.off_bar = off; off += 16;
+  L.off_misc = off; off += 16;
+  L.total = align_up(off, 128);
+  return L;
+}
+
+}  // namespace fnr

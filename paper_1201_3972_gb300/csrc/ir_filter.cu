@@ -1,0 +1,694 @@
+// Host side of the C ABI declared in include/ir_filter.h: argument checks,
+// tensor-map encoding, per-(dtype, k) kernel configuration and tuning,
+// launches, batch plans (explicit CUDA graphs) and error reporting.
+#include "ir_filter.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fnr_params.h"
+
+namespace fnr {
+const void *get_kernel_k3(int esize, int k, int algo);
+const void *get_kernel_k5_7(int esize, int k, int algo);
+const void *get_kernel_k9_11(int esize, int k, int algo);
+const void *get_kernel_k13_15(int esize, int k, int algo);
+const void *get_kernel_k17_21(int esize, int k, int algo);
+
+static const void *get_kernel(int esize, int k, int algo) {
+  if (k == 3) return get_kernel_k3(esize, k, algo);
+  if (k <= 7) return get_kernel_k5_7(esize, k, algo);
+  if (k <= 11) return get_kernel_k9_11(esize, k, algo);
+  if (k <= 15) return get_kernel_k13_15(esize, k, algo);
+  return get_kernel_k17_21(esize, k, algo);
+}
+}  // namespace fnr
+
+using namespace fnr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int esize_of(ir_dtype d) { return d == IR_U8 ? 1 : 2; }
+int kslot(int k) { return (k - 3) / 2; }
+
+bool valid_dtype(int d) { return d == IR_U8 || d == IR_U16 || d == IR_U14; }
+bool valid_k(int k) { return k >= 3 && k <= kMaxK && (k & 1); }
+
+}  // namespace
+
+struct PlanKey {
+  std::vector<unsigned char> bytes;
+  bool operator<(const PlanKey &o) const { return bytes < o.bytes; }
+  bool operator==(const PlanKey &o) const { return bytes == o.bytes; }
+};
+
+struct ir_filter {
+  int device = 0;
+  int sm_count = 0;
+  int max_smem = 0;
+  unsigned *d_status = nullptr;
+  unsigned long long *d_launches = nullptr;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  ir_kernel_config cfg[2][kNumK];
+  std::string last_error;
+  std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, smem) -> CTAs per SM
+  std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
+  std::map<PlanKey, ir_batch_plan *> plans;               // ir_filter_run_batch cache
+  std::vector<PlanKey> plan_order;                        // LRU, oldest first
+};
+
+struct ClassLaunch {
+  int esize = 0, k = 0;
+  ir_kernel_config cfg{};
+  const void *fn = nullptr;
+  int grid = 0, smem = 0;
+  FnrParams prm{};
+};
+
+struct ir_batch_plan {
+  ir_filter *h = nullptr;
+  FrameDev *d_table = nullptr;
+  std::vector<ClassLaunch> classes;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static ir_status fail(ir_filter *h, ir_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  if (h) h->last_error = buf;
+  return s;
+}
+
+#define IR_CUDA(h, call)                                                                     \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((h), IR_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) cudaSetDevice(dev);
+    dev_ = dev;
+  }
+  ~DeviceGuard() {
+    if (prev_ >= 0 && prev_ != dev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = -1, dev_ = 0;
+};
+
+// ---------------------------------------------------------------------------
+// configuration
+// ---------------------------------------------------------------------------
+static ir_kernel_config default_config(int esize, int k) {
+  ir_kernel_config c{};
+  c.ctas_per_sm = 0;
+  if (k == 3) {
+    c.algo = IR_ALGO_DENSE3;
+    c.tile_w = 128;
+    c.tile_h = 32;
+  } else if (k <= 7) {
+    c.algo = IR_ALGO_NETWORK;
+    c.tile_w = 64;
+    c.tile_h = 32;
+  } else {
+    c.algo = IR_ALGO_BITPLANE;
+    c.tile_w = 64;
+    c.tile_h = 32;
+  }
+  (void)esize;
+  return c;
+}
+
+static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_config &c, std::string *why) {
+  auto no = [&](const char *m) {
+    if (why) *why = m;
+    return false;
+  };
+  if (c.tile_w < 8 || c.tile_h < 8 || (c.tile_w % 8) || (c.tile_h % 8)) return no("tile sides must be multiples of 8");
+  // every TMA x coordinate (a multiple of tile_w, minus a 16-byte aligned
+  // halo) and every box row must be a whole number of 16-byte units
+  if ((c.tile_w * esize) % 16) return no("tile_w * bytes per pixel must be a multiple of 16");
+  if (c.algo == IR_ALGO_DENSE3 && k != 3) return no("DENSE3 is the 3x3 window only");
+  if (c.algo == IR_ALGO_NETWORK && k > 7) return no("NETWORK is built for k <= 7");
+  if (c.algo != IR_ALGO_DENSE3 && c.algo != IR_ALGO_NETWORK && c.algo != IR_ALGO_BITPLANE) return no("unknown algo");
+  if (c.ctas_per_sm < 0) return no("ctas_per_sm < 0");
+  const Layout L = make_layout(esize, k, c.algo, c.tile_h, c.tile_w);
+  if (L.bw > 256 || L.bh > 256) return no("tile plus halo exceeds the 256-pixel TMA box");
+  if (c.tile_w > 256 || c.tile_h > 256) return no("tile side > 256");
+  if (h && L.total > h->max_smem) return no("tile needs more shared memory than a CTA can have");
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// frames
+// ---------------------------------------------------------------------------
+static bool ranges_overlap(const void *a, size_t a_len, const void *b, size_t b_len) {
+  const auto pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+  return pa < pb + b_len && pb < pa + a_len;
+}
+
+static ir_status check_frame(ir_filter *h, const void *in, size_t in_pitch, const void *out, size_t out_pitch, int H,
+                             int W, int dtype, int k) {
+  if (!in || !out) return fail(h, IR_EINVAL, "null frame pointer");
+  if (H < 1 || W < 1) return fail(h, IR_EINVAL, "H and W must be >= 1 (got %d x %d)", H, W);
+  if (!valid_dtype(dtype)) return fail(h, IR_EINVAL, "unknown dtype %d", dtype);
+  if (!valid_k(k)) return fail(h, IR_EINVAL, "k must be odd and in [3, %d] (got %d)", kMaxK, k);
+  const size_t row = static_cast<size_t>(W) * esize_of(static_cast<ir_dtype>(dtype));
+  if (in_pitch < row || out_pitch < row) return fail(h, IR_EINVAL, "pitch smaller than W * bytes per pixel");
+  if (static_cast<long long>(H) * W > (1LL << 40)) return fail(h, IR_EINVAL, "frame too large");
+  const size_t in_len = (H - 1) * in_pitch + row, out_len = (H - 1) * out_pitch + row;
+  if (ranges_overlap(in, in_len, out, out_len)) return fail(h, IR_EINVAL, "input and output overlap");
+  return IR_OK;
+}
+
+static bool tma_addressable(const void *p, size_t pitch) {
+  return (reinterpret_cast<uintptr_t>(p) % 16) == 0 && (pitch % 16) == 0 && pitch < (1ull << 40);
+}
+
+static bool encode_map(ir_filter *h, CUtensorMap *map, int esize, const void *base, int H, int W, size_t pitch, int box_w,
+                       int box_h) {
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h)};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = h->encode(map, esize == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                               const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static void make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t in_pitch, void *out, size_t out_pitch,
+                           int H, int W, int esize, int k, const ir_kernel_config &c, unsigned long long *flagged) {
+  std::memset(&f, 0, sizeof f);
+  const int r = (k - 1) / 2;
+  const Layout L = make_layout(esize, k, c.algo, c.tile_h, c.tile_w);
+  f.in = static_cast<const unsigned char *>(in);
+  f.out = static_cast<unsigned char *>(out);
+  f.in_pitch = static_cast<long long>(in_pitch);
+  f.out_pitch = static_cast<long long>(out_pitch);
+  f.H = H;
+  f.W = W;
+  f.tiles_x = (W + c.tile_w - 1) / c.tile_w;
+  f.tiles_y = (H + c.tile_h - 1) / c.tile_h;
+  f.flagged = flagged;
+  f.flags = 0;
+  (void)r;
+  const bool box_ok = (c.tile_w * esize) % 16 == 0 && (L.bw * esize) % 16 == 0;
+  if (box_ok && tma_addressable(in, in_pitch) && encode_map(h, &f.tin, esize, in, H, W, in_pitch, L.bw, L.bh))
+    f.flags |= kFrameTmaIn;
+  if (box_ok && tma_addressable(out, out_pitch) &&
+      encode_map(h, &f.tout, esize, out, H, W, out_pitch, c.tile_w, c.tile_h))
+    f.flags |= kFrameTmaOut;
+}
+
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+static ir_status prepare_class(ir_filter *h, ClassLaunch &cl) {
+  cl.fn = get_kernel(cl.esize, cl.k, cl.cfg.algo);
+  if (!cl.fn) return fail(h, IR_EUNSUPPORTED, "no kernel built for esize=%d k=%d algo=%d", cl.esize, cl.k, cl.cfg.algo);
+  const Layout L = make_layout(cl.esize, cl.k, cl.cfg.algo, cl.cfg.tile_h, cl.cfg.tile_w);
+  cl.smem = L.total;
+  int &attr = h->smem_attr[cl.fn];
+  if (attr < cl.smem) {
+    IR_CUDA(h, cudaFuncSetAttribute(cl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, h->max_smem));
+    attr = h->max_smem;
+  }
+  auto key = std::make_pair(cl.fn, cl.smem);
+  auto it = h->occupancy.find(key);
+  int per_sm = 0;
+  if (it == h->occupancy.end()) {
+    IR_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cl.fn, kThreads, cl.smem));
+    h->occupancy[key] = per_sm;
+  } else {
+    per_sm = it->second;
+  }
+  if (per_sm < 1) return fail(h, IR_EUNSUPPORTED, "kernel does not fit on an SM with %d bytes of shared memory", cl.smem);
+  if (cl.cfg.ctas_per_sm > 0) per_sm = std::min(per_sm, cl.cfg.ctas_per_sm);
+  cl.grid = std::max(1, std::min(cl.prm.total_tiles, per_sm * h->sm_count));
+  return IR_OK;
+}
+
+static ir_status launch_class(ir_filter *h, ClassLaunch &cl, cudaStream_t st) {
+  void *args[] = {&cl.prm};
+  IR_CUDA(h, cudaLaunchKernel(cl.fn, dim3(cl.grid), dim3(kThreads), args, cl.smem, st));
+  return IR_OK;
+}
+
+static ir_status ensure_scratch(ir_filter *h, size_t bytes) {
+  if (h->scratch_bytes >= bytes) return IR_OK;
+  if (h->scratch) {
+    cudaFree(h->scratch);
+    h->scratch = nullptr;
+    h->scratch_bytes = 0;
+  }
+  const size_t want = std::max(bytes, static_cast<size_t>(1) << 20);
+  if (cudaMalloc(&h->scratch, want) != cudaSuccess) {
+    cudaGetLastError();
+    h->scratch = nullptr;
+    return fail(h, IR_ENOMEM, "cannot allocate %zu bytes of scratch", want);
+  }
+  h->scratch_bytes = want;
+  return IR_OK;
+}
+
+static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H, int W,
+                         ir_dtype dtype, int k, cudaStream_t st, unsigned long long *flagged) {
+  ClassLaunch cl;
+  cl.esize = esize_of(dtype);
+  cl.k = k;
+  cl.cfg = h->cfg[cl.esize - 1][kslot(k)];
+  std::memset(&cl.prm, 0, sizeof cl.prm);
+  make_frame_dev(h, cl.prm.single, in, in_pitch, out, out_pitch, H, W, cl.esize, k, cl.cfg, flagged);
+  cl.prm.table = nullptr;
+  cl.prm.nframes = 1;
+  cl.prm.total_tiles = cl.prm.single.tiles_x * cl.prm.single.tiles_y;
+  cl.prm.tile_w = cl.cfg.tile_w;
+  cl.prm.tile_h = cl.cfg.tile_h;
+  cl.prm.status = h->d_status;
+  cl.prm.launches = h->d_launches;
+  ir_status s = prepare_class(h, cl);
+  if (s != IR_OK) return s;
+  if (flagged) IR_CUDA(h, cudaMemsetAsync(flagged, 0, sizeof(unsigned long long), st));
+  return launch_class(h, cl, st);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *ir_filter_version(void) { return "0.1.0"; }
+
+const char *ir_status_string(ir_status s) {
+  switch (s) {
+    case IR_OK: return "ok";
+    case IR_EINVAL: return "invalid argument";
+    case IR_EALIGN: return "misaligned frame";
+    case IR_ENOMEM: return "out of device memory";
+    case IR_ECUDA: return "CUDA error";
+    case IR_ETIMEOUT: return "device-side wait timed out";
+    case IR_EBUSY: return "busy";
+    case IR_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char *ir_filter_last_error(const ir_filter *h) { return h ? h->last_error.c_str() : g_last_error.c_str(); }
+
+ir_status ir_filter_create(ir_filter **out, int device) {
+  if (!out) return fail(nullptr, IR_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, IR_EINVAL, "no CUDA device %d", device);
+  }
+  DeviceGuard g(device);
+  std::unique_ptr<ir_filter> h(new ir_filter());
+  h->device = device;
+  IR_CUDA(nullptr, cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device));
+  IR_CUDA(nullptr, cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return fail(nullptr, IR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  }
+  h->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  IR_CUDA(nullptr, cudaMalloc(&h->d_status, sizeof(unsigned)));
+  IR_CUDA(nullptr, cudaMalloc(&h->d_launches, sizeof(unsigned long long)));
+  IR_CUDA(nullptr, cudaMemset(h->d_status, 0, sizeof(unsigned)));
+  IR_CUDA(nullptr, cudaMemset(h->d_launches, 0, sizeof(unsigned long long)));
+  for (int e = 1; e <= 2; ++e)
+    for (int k = 3; k <= kMaxK; k += 2) h->cfg[e - 1][kslot(k)] = default_config(e, k);
+  *out = h.release();
+  return IR_OK;
+}
+
+void ir_batch_plan_destroy(ir_batch_plan *plan);
+
+void ir_filter_destroy(ir_filter *h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  for (auto &kv : h->plans) ir_batch_plan_destroy(kv.second);
+  h->plans.clear();
+  if (h->scratch) cudaFree(h->scratch);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->d_launches) cudaFree(h->d_launches);
+  delete h;
+}
+
+ir_status ir_filter_run2(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H, int W,
+                         ir_dtype dtype, int k, void *cuda_stream, unsigned long long *flagged_count) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
+  if (s != IR_OK) return s;
+  DeviceGuard g(h->device);
+  return run_one(h, in, in_pitch, out, out_pitch, H, W, dtype, k, static_cast<cudaStream_t>(cuda_stream),
+                 flagged_count);
+}
+
+ir_status ir_filter_run(ir_filter *h, void *frame, int H, int W, size_t pitch_bytes, ir_dtype dtype, int k,
+                        void *cuda_stream) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (!frame) return fail(h, IR_EINVAL, "null frame pointer");
+  if (H < 1 || W < 1 || !valid_dtype(dtype)) return check_frame(h, frame, pitch_bytes, frame, pitch_bytes, H, W, dtype, k);
+  DeviceGuard g(h->device);
+  const int es = esize_of(dtype);
+  const size_t row = static_cast<size_t>(W) * es;
+  const size_t spitch = (row + 255) / 256 * 256;
+  ir_status s = ensure_scratch(h, spitch * static_cast<size_t>(H));
+  if (s != IR_OK) return s;
+  s = check_frame(h, h->scratch, spitch, frame, pitch_bytes, H, W, dtype, k);
+  if (s != IR_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  IR_CUDA(h, cudaMemcpy2DAsync(h->scratch, spitch, frame, pitch_bytes, row, H, cudaMemcpyDeviceToDevice, st));
+  return run_one(h, h->scratch, spitch, frame, pitch_bytes, H, W, dtype, k, st, nullptr);
+}
+
+ir_status ir_filter_sync_status(ir_filter *h) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  DeviceGuard g(h->device);
+  IR_CUDA(h, cudaDeviceSynchronize());
+  unsigned st = 0;
+  IR_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost));
+  IR_CUDA(h, cudaMemset(h->d_status, 0, sizeof st));
+  if (st & kStatusTimeout) return fail(h, IR_ETIMEOUT, "a bounded device-side wait gave up");
+  return IR_OK;
+}
+
+unsigned long long ir_filter_launch_count(const ir_filter *h) {
+  if (!h) return 0;
+  DeviceGuard g(h->device);
+  unsigned long long n = 0;
+  if (cudaMemcpy(&n, h->d_launches, sizeof n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+ir_status ir_filter_get_config(ir_filter *h, ir_dtype dtype, int k, ir_kernel_config *out) {
+  if (!h || !out) return fail(h, IR_EINVAL, "null argument");
+  if (!valid_dtype(dtype) || !valid_k(k)) return fail(h, IR_EINVAL, "bad dtype or k");
+  *out = h->cfg[esize_of(dtype) - 1][kslot(k)];
+  return IR_OK;
+}
+
+ir_status ir_filter_set_config(ir_filter *h, ir_dtype dtype, int k, const ir_kernel_config *cfg) {
+  if (!h || !cfg) return fail(h, IR_EINVAL, "null argument");
+  if (!valid_dtype(dtype) || !valid_k(k)) return fail(h, IR_EINVAL, "bad dtype or k");
+  ir_kernel_config c = *cfg;
+  const int es = esize_of(dtype);
+  if (c.algo == IR_ALGO_AUTO) c = default_config(es, k);
+  std::string why;
+  if (!config_ok(h, es, k, c, &why)) return fail(h, IR_EINVAL, "config rejected: %s", why.c_str());
+  if (!get_kernel(es, k, c.algo)) return fail(h, IR_EUNSUPPORTED, "algo %d not built for k=%d", c.algo, k);
+  h->cfg[es - 1][kslot(k)] = c;
+  return IR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch plans
+// ---------------------------------------------------------------------------
+ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, ir_batch_plan **out) {
+  if (!h || !out) return fail(h, IR_EINVAL, "null argument");
+  *out = nullptr;
+  if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
+  for (int i = 0; i < n; ++i) {
+    const ir_frame_desc &d = descs[i];
+    ir_status s = check_frame(h, d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, d.dtype, d.k);
+    if (s != IR_OK) return fail(h, s, "frame %d: %s", i, h->last_error.c_str());
+  }
+  // outputs must not overlap any input of the batch (frames run concurrently)
+  for (int i = 0; i < n; ++i) {
+    const size_t orow = static_cast<size_t>(descs[i].W) * esize_of(descs[i].dtype);
+    const size_t olen = (descs[i].H - 1) * descs[i].out_pitch + orow;
+    for (int j = 0; j < n; ++j) {
+      const size_t irow = static_cast<size_t>(descs[j].W) * esize_of(descs[j].dtype);
+      const size_t ilen = (descs[j].H - 1) * descs[j].in_pitch + irow;
+      if (ranges_overlap(descs[i].out, olen, descs[j].in, ilen))
+        return fail(h, IR_EINVAL, "output of frame %d overlaps input of frame %d", i, j);
+    }
+  }
+  DeviceGuard g(h->device);
+  std::unique_ptr<ir_batch_plan> plan(new ir_batch_plan());
+  plan->h = h;
+  // group by (esize, k): one persistent launch per class
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) groups[{esize_of(descs[i].dtype), descs[i].k}].push_back(i);
+  std::vector<FrameDev> host(n);
+  int slot = 0;
+  std::vector<std::pair<int, int>> ranges;  // (first slot, count) per class
+  for (auto &kv : groups) {
+    ClassLaunch cl;
+    cl.esize = kv.first.first;
+    cl.k = kv.first.second;
+    cl.cfg = h->cfg[cl.esize - 1][kslot(cl.k)];
+    int tiles = 0;
+    const int first = slot;
+    for (int i : kv.second) {
+      const ir_frame_desc &d = descs[i];
+      make_frame_dev(h, host[slot], d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, cl.esize, cl.k, cl.cfg,
+                     d.flagged_count);
+      host[slot].tile_begin = tiles;
+      tiles += host[slot].tiles_x * host[slot].tiles_y;
+      ++slot;
+    }
+    std::memset(&cl.prm, 0, sizeof cl.prm);
+    cl.prm.nframes = static_cast<int>(kv.second.size());
+    cl.prm.total_tiles = tiles;
+    cl.prm.tile_w = cl.cfg.tile_w;
+    cl.prm.tile_h = cl.cfg.tile_h;
+    cl.prm.status = h->d_status;
+    cl.prm.launches = h->d_launches;
+    ir_status s = prepare_class(h, cl);
+    if (s != IR_OK) return s;
+    plan->classes.push_back(cl);
+    ranges.emplace_back(first, cl.prm.nframes);
+  }
+  IR_CUDA(h, cudaMalloc(&plan->d_table, sizeof(FrameDev) * n));
+  IR_CUDA(h, cudaMemcpy(plan->d_table, host.data(), sizeof(FrameDev) * n, cudaMemcpyHostToDevice));
+  for (size_t c = 0; c < plan->classes.size(); ++c) plan->classes[c].prm.table = plan->d_table + ranges[c].first;
+
+  // explicit graph: counter memsets first, then one kernel node per class
+  IR_CUDA(h, cudaGraphCreate(&plan->graph, 0));
+  std::vector<cudaGraphNode_t> memsets;
+  std::vector<unsigned long long *> counters;
+  for (int i = 0; i < n; ++i)
+    if (descs[i].flagged_count &&
+        std::find(counters.begin(), counters.end(), descs[i].flagged_count) == counters.end())
+      counters.push_back(descs[i].flagged_count);
+  for (unsigned long long *ctr : counters) {
+    cudaMemsetParams mp{};
+    mp.dst = ctr;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    mp.pitch = 0;
+    mp.value = 0;
+    cudaGraphNode_t node;
+    IR_CUDA(h, cudaGraphAddMemsetNode(&node, plan->graph, nullptr, 0, &mp));
+    memsets.push_back(node);
+  }
+  for (ClassLaunch &cl : plan->classes) {
+    void *args[] = {&cl.prm};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(cl.fn);
+    kp.gridDim = dim3(cl.grid);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = static_cast<unsigned>(cl.smem);
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    cudaGraphNode_t node;
+    IR_CUDA(h, cudaGraphAddKernelNode(&node, plan->graph, memsets.empty() ? nullptr : memsets.data(), memsets.size(),
+                                      &kp));
+  }
+  IR_CUDA(h, cudaGraphInstantiate(&plan->exec, plan->graph, 0));
+  *out = plan.release();
+  return IR_OK;
+}
+
+ir_status ir_batch_plan_launch(ir_batch_plan *plan, void *cuda_stream) {
+  if (!plan) return fail(nullptr, IR_EINVAL, "null plan");
+  DeviceGuard g(plan->h->device);
+  IR_CUDA(plan->h, cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(cuda_stream)));
+  return IR_OK;
+}
+
+int ir_batch_plan_kernel_count(const ir_batch_plan *plan) {
+  return plan ? static_cast<int>(plan->classes.size()) : 0;
+}
+
+void ir_batch_plan_destroy(ir_batch_plan *plan) {
+  if (!plan) return;
+  DeviceGuard g(plan->h->device);
+  if (plan->exec) cudaGraphExecDestroy(plan->exec);
+  if (plan->graph) cudaGraphDestroy(plan->graph);
+  if (plan->d_table) cudaFree(plan->d_table);
+  delete plan;
+}
+
+ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, void *cuda_stream) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
+  PlanKey key;
+  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg));
+  std::memcpy(key.bytes.data(), descs, sizeof(ir_frame_desc) * n);
+  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n, h->cfg, sizeof(h->cfg));
+  auto it = h->plans.find(key);
+  ir_batch_plan *plan = nullptr;
+  if (it != h->plans.end()) {
+    plan = it->second;
+    auto pos = std::find(h->plan_order.begin(), h->plan_order.end(), key);
+    if (pos != h->plan_order.end()) h->plan_order.erase(pos);
+    h->plan_order.push_back(key);
+  } else {
+    ir_status s = ir_batch_plan_create(h, descs, n, &plan);
+    if (s != IR_OK) return s;
+    constexpr size_t kMaxPlans = 8;
+    if (h->plans.size() >= kMaxPlans) {
+      // the oldest plan may still be in flight on some stream: wait before freeing it
+      DeviceGuard g(h->device);
+      cudaDeviceSynchronize();
+      ir_batch_plan_destroy(h->plans[h->plan_order.front()]);
+      h->plans.erase(h->plan_order.front());
+      h->plan_order.erase(h->plan_order.begin());
+    }
+    h->plans[key] = plan;
+    h->plan_order.push_back(key);
+  }
+  return ir_batch_plan_launch(plan, cuda_stream);
+}
+
+// ---------------------------------------------------------------------------
+// tuning
+// ---------------------------------------------------------------------------
+static std::vector<ir_kernel_config> candidates(int esize, int k) {
+  std::vector<ir_kernel_config> out;
+  auto add = [&](int algo, int tw, int th) { out.push_back(ir_kernel_config{tw, th, algo, 0}); };
+  if (k == 3) {
+    for (int tw : {64, 128, 192})
+      for (int th : {16, 32, 64}) add(IR_ALGO_DENSE3, tw, th);
+    add(IR_ALGO_NETWORK, 64, 32);
+    add(IR_ALGO_BITPLANE, 64, 32);
+  } else if (k <= 7) {
+    for (int tw : {32, 64, 128})
+      for (int th : {16, 32}) add(IR_ALGO_NETWORK, tw, th);
+    add(IR_ALGO_BITPLANE, 64, 32);
+    add(IR_ALGO_BITPLANE, 128, 32);
+  } else {
+    for (int tw : {32, 64, 128})
+      for (int th : {16, 32, 64}) add(IR_ALGO_BITPLANE, tw, th);
+  }
+  (void)esize;
+  return out;
+}
+
+// Host-side synthetic tuning frame: smooth ramp plus 10% salt-and-pepper
+// (a small LCG; only the timing depends on it).
+static void tuning_frame(std::vector<unsigned char> &buf, int H, int W, int esize, size_t pitch) {
+  buf.assign(pitch * H, 0);
+  uint64_t s = 0x9e3779b97f4a7c15ull;
+  auto next = [&]() {
+    s = s * 6364136223846793005ull + 1442695040888963407ull;
+    return static_cast<uint32_t>(s >> 33);
+  };
+  const uint32_t maxv = esize == 1 ? 255u : 16383u;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      uint32_t v = (static_cast<uint32_t>(x + y) * (maxv / 4)) / static_cast<uint32_t>(W + H) + maxv / 4 + (next() % 9);
+      const uint32_t u = next() % 100;
+      if (u < 5) v = 0;
+      else if (u < 10) v = maxv;
+      if (esize == 1) buf[y * pitch + x] = static_cast<unsigned char>(v);
+      else std::memcpy(&buf[y * pitch + 2 * x], &v, 2);
+    }
+}
+
+ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, void *cuda_stream) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (!valid_dtype(dtype) || !valid_k(k) || H < 1 || W < 1) return fail(h, IR_EINVAL, "bad tuning arguments");
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int es = esize_of(dtype);
+  const size_t pitch = (static_cast<size_t>(W) * es + 255) / 256 * 256;
+  std::vector<unsigned char> hbuf;
+  tuning_frame(hbuf, H, W, es, pitch);
+  void *din = nullptr, *dout = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ir_status result = IR_OK;
+  ir_kernel_config best = h->cfg[es - 1][kslot(k)];
+  const ir_kernel_config saved = best;
+  float best_ms = 1e30f;
+  do {
+    if (cudaMalloc(&din, pitch * H) != cudaSuccess || cudaMalloc(&dout, pitch * H) != cudaSuccess) {
+      cudaGetLastError();
+      result = fail(h, IR_ENOMEM, "cannot allocate tuning frames");
+      break;
+    }
+    if (cudaMemcpy(din, hbuf.data(), pitch * H, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      result = fail(h, IR_ECUDA, "tuning setup failed");
+      break;
+    }
+    for (const ir_kernel_config &c : candidates(es, k)) {
+      if (!config_ok(h, es, k, c, nullptr) || !get_kernel(es, k, c.algo)) continue;
+      h->cfg[es - 1][kslot(k)] = c;
+      bool bad = false;
+      for (int w = 0; w < 2 && !bad; ++w)
+        bad = run_one(h, din, pitch, dout, pitch, H, W, dtype, k, st, nullptr) != IR_OK;
+      if (bad) continue;
+      const int reps = 5;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && !bad; ++r) bad = run_one(h, din, pitch, dout, pitch, H, W, dtype, k, st, nullptr) != IR_OK;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess || bad) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  } while (false);
+  h->cfg[es - 1][kslot(k)] = (result == IR_OK && best_ms < 1e30f) ? best : saved;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (din) cudaFree(din);
+  if (dout) cudaFree(dout);
+  return result;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+"""CPU-only checks of the C-ABI library and of the generated selection networks.
+
+No compute call runs here (there is no GPU): the library must build, load,
+export every entry point that include/ir_filter.h declares, and fail cleanly.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1201_3972_gb300 import _build, _lib
+from paper_1201_3972_gb300.csrc import gen_networks as gn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ir_filter.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(ir_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("ir_filter_create", "ir_filter_run", "ir_filter_destroy", "ir_filter_run2",
+                 "ir_filter_run_batch"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(_lib.EXPORTED)
+
+
+def test_status_strings_and_version(lib):
+    assert lib.ir_filter_version() == b"0.1.0"
+    for s in range(8):
+        assert lib.ir_status_string(s)
+    assert lib.ir_status_string(0) == b"ok"
+
+
+def test_create_without_device_fails_cleanly(lib):
+    h = ctypes.c_void_p()
+    st = lib.ir_filter_create(ctypes.byref(h), 0 if not _has_gpu() else 10_000)
+    assert st == _lib.IR_EINVAL
+    assert not h.value
+    assert lib.ir_filter_last_error(None)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.ir_filter_run(None, None, 1, 1, 1, 0, 3, None) == _lib.IR_EINVAL
+    assert lib.ir_filter_run2(None, None, 1, None, 1, 1, 1, 0, 3, None, None) == _lib.IR_EINVAL
+    assert lib.ir_filter_run_batch(None, None, 0, None) == _lib.IR_EINVAL
+    assert lib.ir_filter_sync_status(None) == _lib.IR_EINVAL
+    assert lib.ir_filter_launch_count(None) == 0
+    lib.ir_filter_destroy(None)
+    lib.ir_batch_plan_destroy(None)
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError):
+        _lib.load(str(tmp_path / "missing.so"))
+
+
+# ---------------------------------------------------------------------------
+# selection networks (0-1 principle)
+# ---------------------------------------------------------------------------
+def _zero_one_check(net, out, n, m, chunk_bits=20):
+    """Evaluate the network on all 2^n 0-1 inputs (in chunks, vectorised).
+    For a 0-1 input the rank-m element is 0 exactly when more than m inputs
+    are 0, so wire `out` must equal (number of zeros <= m)."""
+    total = 1 << n
+    step = 1 << min(chunk_bits, n)
+    for start in range(0, total, step):
+        idx = np.arange(start, start + step, dtype=np.uint64)
+        wires = [((idx >> np.uint64(i)) & np.uint64(1)).astype(bool) for i in range(n)]
+        ones = np.bitwise_count(idx).astype(np.int64)
+        for a, b, _, _ in net:
+            wires[a], wires[b] = wires[a] & wires[b], wires[a] | wires[b]
+        if not np.array_equal(wires[out], (n - ones) <= m):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_median_network_zero_one_principle(k):
+    net, out = gn.median_network(k)
+    n = k * k
+    assert _zero_one_check(net, out, n, (n - 1) // 2)
+
+
+@pytest.mark.parametrize("k", [7, 9])
+def test_median_network_random(k):
+    net, out = gn.median_network(k)
+    n = k * k
+    rng = np.random.default_rng(k)
+    for _ in range(3000):
+        v = rng.integers(0, 6, n).tolist()
+        assert gn.apply(net, v)[out] == sorted(v)[(n - 1) // 2]
+
+
+def test_generated_header_is_current():
+    with open(gn.HEADER) as fh:
+        assert fh.read() == gn.emit()
+
+
+def test_dense3_identity_zero_one():
+    """The DENSE3 kernel takes g_m = med3(max(lo), med3(mid), min(hi)) of the
+    three vertically sorted columns; check that identity on all 2^9 0-1
+    windows (0-1 principle for the min/max circuit it forms)."""
+    for bits in range(1 << 9):
+        w = [(bits >> i) & 1 for i in range(9)]
+        cols = [sorted(w[j::3]) for j in range(3)]
+        lo = [c[0] for c in cols]
+        md = [c[1] for c in cols]
+        hi = [c[2] for c in cols]
+        med = sorted([max(lo), sorted(md)[1], min(hi)])[1]
+        assert med == sorted(w)[4]
+        assert min(lo) == min(w) and max(hi) == max(w)

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit for bit.
+
+Every test calls the library through its C ABI (ctypes binding) on device
+buffers and compares every output pixel, and the flagged count, with the
+oracle on the same seeded input. Sizes span several tiles plus ragged tails;
+the workload tests run the full frame sizes the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _dev import download, empty_like_frame, guard_bytes_intact, upload
+from _golden import all_fixtures
+from paper_1201_3972_gb300 import _lib, synth
+
+pytestmark = pytest.mark.gpu
+
+ALL_K = tuple(range(3, 22, 2))
+
+
+@pytest.fixture(scope="module")
+def flt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1201_3972_gb300 import _build
+    _build.build()
+    f = _lib.Filter(0)
+    yield f
+    f.sync_status()
+    f.close()
+
+
+def algos_for(k):
+    out = [_lib.IR_ALGO_BITPLANE]
+    if k <= 7:
+        out.append(_lib.IR_ALGO_NETWORK)
+    if k == 3:
+        out.append(_lib.IR_ALGO_DENSE3)
+    return out
+
+
+def tiles_for(es, k):
+    r = (k - 1) // 2
+    xoff = -(-r // (16 // es)) * (16 // es)
+    out = []
+    for tw, th in ((64, 32), (128, 16), (32, 8), (8, 8), (16, 8), (128, 64), (192, 16)):
+        if tw + 2 * xoff <= 256 and th + 2 * r <= 256 and (tw * es) % 16 == 0:
+            out.append((tw, th))
+    return out
+
+
+def dtype_code(frame, u14=False):
+    return _lib.IR_U8 if frame.dtype == np.uint8 else (_lib.IR_U14 if u14 else _lib.IR_U16)
+
+
+def gpu_fnr(flt, frame, k, u14=False, in_pitch=None, out_pitch=None, in_off=0, out_off=0, count=True):
+    """Run ir_filter_run2 on a copy of `frame`; returns (output, flagged)."""
+    import torch
+    H, W = frame.shape
+    ib, ia, ip = upload(frame, in_pitch, in_off)
+    ob, oa, op = empty_like_frame(frame, out_pitch, out_off)
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda") if count else None
+    flt.ir_filter_run2(ia, ip, oa, op, H, W, dtype_code(frame, u14), k, None, ctr)
+    out = download(ob, oa, op, H, W, frame.dtype)
+    assert guard_bytes_intact(ob, oa, op, H, W, frame.itemsize), "write outside the frame"
+    flagged = int(ctr.item()) if count else None
+    return out, flagged
+
+
+def check(flt, frame, k, **kw):
+    want, wf = oracle.fnr(frame, k)
+    got, gf = gpu_fnr(flt, frame, k, **kw)
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        y, x = bad[0]
+        raise AssertionError(f"k={k} {frame.shape} {frame.dtype}: {len(bad)} pixels differ; first at "
+                             f"({y},{x}) got {got[y, x]} want {want[y, x]}")
+    if gf is not None:
+        assert gf == wf, f"flagged {gf} != oracle {wf}"
+
+
+def with_config(flt, dtype, k, algo, tw, th):
+    flt.set_config(dtype, k, tw, th, algo)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("fx", all_fixtures(), ids=lambda f: f["name"])
+def test_golden_fixtures_every_algo(flt, fx):
+    k = fx["k"]
+    es = fx["input"].itemsize
+    for algo in algos_for(k):
+        for dt in ((_lib.IR_U8,) if es == 1 else (_lib.IR_U16, _lib.IR_U14)):
+            with_config(flt, dt, k, algo, 64, 32)
+        got, gf = gpu_fnr(flt, fx["input"], k, u14=(fx["dtype"] == _lib.IR_U14))
+        np.testing.assert_array_equal(got, fx["output"])
+        assert gf == fx["flagged"]
+    flt.set_config(_lib.IR_U8, k, 0, 0, _lib.IR_ALGO_AUTO)
+    flt.set_config(_lib.IR_U16, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+@pytest.mark.parametrize("k", ALL_K)
+@pytest.mark.parametrize("es", [1, 2])
+def test_every_algo_and_tile_random(flt, k, es):
+    """Uniform random and tie-heavy frames, every (algo, tile) built for k,
+    ragged sizes that are not multiples of any tile side."""
+    rng = np.random.default_rng(1000 * k + es)
+    dt = _lib.IR_U8 if es == 1 else _lib.IR_U16
+    npdt = np.uint8 if es == 1 else np.uint16
+    maxv = 255 if es == 1 else 65535
+    shapes = [(67, 150), (33, 29)]
+    for algo in algos_for(k):
+        for tw, th in tiles_for(es, k):
+            flt.set_config(dt, k, tw, th, algo)
+            for H, W in shapes:
+                a = rng.integers(0, maxv + 1, (H, W)).astype(npdt)
+                check(flt, a, k)
+                b = rng.choice([0, 1, maxv // 2, maxv], (H, W)).astype(npdt)
+                check(flt, b, k)
+    flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 9, 15, 21])
+def test_edge_shapes(flt, k):
+    """1x1, single rows and columns, frames smaller than the window, odd
+    widths, for both pixel types and every algo."""
+    rng = np.random.default_rng(k)
+    for es, dt in ((1, _lib.IR_U8), (2, _lib.IR_U16)):
+        npdt = np.uint8 if es == 1 else np.uint16
+        for algo in algos_for(k):
+            flt.set_config(dt, k, 64, 32, algo)
+            for H, W in ((1, 1), (1, 7), (7, 1), (1, 300), (300, 1), (2, 3), (k - 1, k + 2), (5, 17), (9, 130)):
+                a = rng.integers(0, 256 if es == 1 else 65536, (H, W)).astype(npdt)
+                check(flt, a, k)
+        flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+@pytest.mark.parametrize("k", [3, 5, 9, 21])
+def test_unaligned_pitch_and_base(flt, k):
+    """Odd pitches and misaligned bases take the plain-load / plain-store path;
+    aligned-in/unaligned-out and the reverse mix TMA and plain paths."""
+    rng = np.random.default_rng(7 + k)
+    for npdt in (np.uint8, np.uint16):
+        maxv = np.iinfo(npdt).max
+        a = rng.integers(0, maxv + 1, (70, 133)).astype(npdt)
+        check(flt, a, k, in_pitch=137, out_pitch=141)
+        check(flt, a, k, in_off=1, out_off=3, in_pitch=160, out_pitch=160)
+        check(flt, a, k, in_pitch=144, out_pitch=139)
+        check(flt, a, k, in_pitch=139, out_pitch=144)
+
+
+def test_in_place_run_matches_oracle(flt):
+    import torch
+    for s in (synth.workload_single_u8()[0], synth.workload_sweep_u14()[4]):
+        f = s.make()
+        want, _ = oracle.fnr(f, s.k)
+        buf, addr, pitch = upload(f)
+        flt.ir_filter_run(addr, f.shape[0], f.shape[1], pitch, s.dtype, s.k)
+        torch.cuda.synchronize()
+        got = download(buf, addr, pitch, f.shape[0], f.shape[1], f.dtype)
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("spec", synth.workload_single_u8() + synth.workload_sweep_u14(), ids=lambda s: s.tag)
+def test_workload_small_k_full_size(flt, spec):
+    """320x240 u8 (3x3) and the 640x512 14-bit sweep (5-40% impulses, 3/5/7),
+    full frames, every algo."""
+    f = spec.make()
+    want, wf = oracle.fnr(f, spec.k)
+    for algo in algos_for(spec.k):
+        flt.set_config(spec.dtype, spec.k, 64 if algo != _lib.IR_ALGO_DENSE3 else 128, 32, algo)
+        got, gf = gpu_fnr(flt, f, spec.k, u14=spec.dtype == _lib.IR_U14)
+        np.testing.assert_array_equal(got, want)
+        assert gf == wf
+    flt.set_config(spec.dtype, spec.k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+@pytest.mark.parametrize("spec", synth.workload_large_k(), ids=lambda s: s.tag)
+def test_workload_large_k_full_size(flt, spec):
+    """1280x1024 14-bit, 20% random-valued impulses, windows 9-21."""
+    f = spec.make()
+    want, wf = oracle.fnr_mt(f, spec.k, 16)
+    got, gf = gpu_fnr(flt, f, spec.k, u14=True)
+    np.testing.assert_array_equal(got, want)
+    assert gf == wf
+
+
+def test_errors_are_reported(flt):
+    import torch
+    a = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    addr = int(a.data_ptr())
+    for k in (2, 1, 23, 0, -3):
+        with pytest.raises(_lib.IrError) as e:
+            flt.ir_filter_run2(addr, 8, addr + 32, 8, 2, 8, _lib.IR_U8, k)
+        assert e.value.status == _lib.IR_EINVAL
+    with pytest.raises(_lib.IrError):
+        flt.ir_filter_run2(addr, 8, addr + 4, 8, 2, 8, _lib.IR_U8, 3)      # overlap
+    with pytest.raises(_lib.IrError):
+        flt.ir_filter_run2(addr, 4, addr + 32, 8, 2, 8, _lib.IR_U8, 3)      # pitch < W
+    with pytest.raises(_lib.IrError):
+        flt.ir_filter_run2(0, 8, addr + 32, 8, 2, 8, _lib.IR_U8, 3)         # null
+    with pytest.raises(_lib.IrError):
+        flt.ir_filter_run2(addr, 8, addr + 32, 8, 0, 8, _lib.IR_U8, 3)      # H = 0
+    with pytest.raises(_lib.IrError):
+        flt.set_config(_lib.IR_U8, 5, 64, 32, _lib.IR_ALGO_DENSE3)          # dense3 is k=3 only
+    with pytest.raises(_lib.IrError):
+        flt.set_config(_lib.IR_U8, 3, 250, 32, _lib.IR_ALGO_DENSE3)         # box > 256
+    flt.sync_status()
+
+
+def test_autotune_keeps_results_exact(flt):
+    f = synth.workload_sweep_u14()[1].make()
+    for k in (3, 5, 9):
+        flt.autotune(_lib.IR_U14, k, 512, 640)
+        cfg = flt.get_config(_lib.IR_U14, k)
+        assert cfg["algo"] in (_lib.IR_ALGO_DENSE3, _lib.IR_ALGO_NETWORK, _lib.IR_ALGO_BITPLANE)
+        check(flt, f, k, u14=True)
+        flt.set_config(_lib.IR_U14, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+def test_launch_counter_counts_kernels(flt):
+    before = flt.launch_count()
+    f = synth.workload_single_u8()[0].make()
+    for _ in range(3):
+        gpu_fnr(flt, f, 3, count=False)
+    assert flt.launch_count() - before == 3
