@@ -240,18 +240,17 @@ __device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
 // (hi lane of a, lo lane of b): the odd-aligned pair between two even pairs.
 __device__ __forceinline__ uint32_t odd_pair(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5432); }
 
-// Keep-mask per 16-bit lane: 0xffff where g_min < c < g_max (signal pixel),
-// 0 where c equals g_min or g_max (noisy). c - g_min and g_max - c never borrow
-// across lanes because every lane satisfies g_min <= c <= g_max.
-__device__ __forceinline__ uint32_t signal_mask(uint32_t c, uint32_t gmin, uint32_t gmax, int &flagged) {
-  const uint32_t z = vmin2(c - gmin, gmax - c);
-  const uint32_t nz = vmin2(z, 0x00010001u);
-  flagged += 2 - __popc(nz);
-  return nz * 0xffffu;
+// Per 16-bit lane: 1 where g_min < c < g_max (signal pixel), 0 where c equals
+// g_min or g_max (noisy). c - g_min and g_max - c never borrow across lanes
+// because every lane satisfies g_min <= c <= g_max.
+__device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint32_t gmax) {
+  return vmin2(vmin2(c - gmin, gmax - c), 0x00010001u);
 }
 
+// tw_valid, th_valid: the part of the tile inside the frame (only those
+// pixels are counted as flagged; the rest is never stored).
 template <typename T>
-__device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int &flagged) {
+__device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int tw_valid, int th_valid, int &flagged) {
   constexpr int XOFF = xoff_for(1, sizeof(T));
   const int segs = TW >> 3;
   const int items = (TH >> 1) * segs;
@@ -293,8 +292,12 @@ __device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int &flagg
         const uint32_t gmax = vmax2(vmax2(ohi[pp], mhi), ohi[pp + 1]);
         const uint32_t gm = med3v(maxlo, medmd, minhi);
         const uint32_t c = e[1 + o][pp + 1];
-        const uint32_t keep = signal_mask(c, gmin, gmax, flagged);
+        const uint32_t sig = signal_bits(c, gmin, gmax);
+        const uint32_t keep = sig * 0xffffu;
         res[pp] = (c & keep) | (gm & ~keep);
+        const int col = tx + 2 * pp;
+        const uint32_t valid = (ty + o < th_valid) ? ((col < tw_valid ? 1u : 0u) | (col + 1 < tw_valid ? 0x10000u : 0u)) : 0u;
+        flagged += __popc((sig ^ 0x00010001u) & valid);
       }
       store_row8<T>(O + (ty + o) * TW + tx, res);
     }
@@ -366,7 +369,8 @@ __device__ void vertical_pass(const T *S, uint16_t *vmin, uint16_t *vmax, int TW
 // list length accumulates in *count.
 template <typename T, int K>
 __device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uint16_t *vmax, T *O,
-                                     uint16_t *list, unsigned *count, int TW, int TH, int BW, int VW) {
+                                     uint16_t *list, unsigned *count, int TW, int TH, int BW, int VW, int tw_valid,
+                                     int th_valid) {
   constexpr int R = (K - 1) / 2, RG = RowGroup<K>::value;
   constexpr int XOFF = xoff_for(R, sizeof(T));
   const int per_row = TW / RG;
@@ -393,7 +397,8 @@ __device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uin
       for (int q = 0; q < RG; ++q) {
         const uint32_t c = crow[q];
         O[ty * TW + tx0 + q] = static_cast<T>(c);
-        fm |= static_cast<uint32_t>(c == gmin[q] || c == gmax[q]) << q;
+        const bool inside = ty < th_valid && tx0 + q < tw_valid;
+        fm |= static_cast<uint32_t>(inside && (c == gmin[q] || c == gmax[q])) << q;
       }
     }
     // warp-aggregated append
@@ -562,7 +567,11 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
     const int x0 = tile_x * TW, y0 = tile_y * TH;
     const int xs = x0 - XOFF, ys = y0 - R;
     const bool tma_in = (cf->flags & kFrameTmaIn) != 0;
-    const bool tma_out = (cf->flags & kFrameTmaOut) != 0;
+    // A TMA store clips the box at the frame edge in whole 16-byte units, so a
+    // right-edge tile of a frame whose row is not a multiple of 16 bytes would
+    // touch the bytes between W and the pitch: such tiles use plain stores.
+    const bool ragged_right = x0 + TW > cf->W && ((cf->W * E) & 15) != 0;
+    const bool tma_out = (cf->flags & kFrameTmaOut) != 0 && !ragged_right;
     T *const S = s ? stage1 : stage0;
     T *const O = s ? out1 : out0;
 
@@ -589,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
 
     if constexpr (ALGO == ALGO_DENSE3) {
       int flagged = 0;
-      dense3_tile<T>(S, O, TW, TH, BW, flagged);
+      dense3_tile<T>(S, O, TW, TH, BW, cf->W - x0, cf->H - y0, flagged);
       if (cf->flagged != nullptr) {
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if ((tid & 31) == 0 && flagged) atomicAdd(&misc[0], static_cast<unsigned>(flagged));
@@ -603,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
       }
       vertical_pass<T, K>(S, vmin, vmax, TW, TH, BW, L.vw);
       __syncthreads();
-      horizontal_flag_pass<T, K>(S, vmin, vmax, O, list, &misc[0], TW, TH, BW, L.vw);
+      horizontal_flag_pass<T, K>(S, vmin, vmax, O, list, &misc[0], TW, TH, BW, L.vw, cf->W - x0, cf->H - y0);
       __syncthreads();
       const int F = static_cast<int>(misc[0]);
       if constexpr (ALGO == ALGO_NETWORK) {

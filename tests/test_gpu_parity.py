@@ -146,6 +146,10 @@ def test_unaligned_pitch_and_base(flt, k):
         check(flt, a, k, in_off=1, out_off=3, in_pitch=160, out_pitch=160)
         check(flt, a, k, in_pitch=144, out_pitch=139)
         check(flt, a, k, in_pitch=139, out_pitch=144)
+        # 16-byte aligned pitch, row of W*e bytes not a multiple of 16: the
+        # bytes between W and the pitch belong to the caller
+        check(flt, a, k, in_pitch=144, out_pitch=144)
+        check(flt, a[:, :129].copy(), k, in_pitch=256, out_pitch=256)
 
 
 def test_in_place_run_matches_oracle(flt):
