@@ -58,7 +58,7 @@ typedef enum { IR_U8 = 0, IR_U16 = 1, IR_U14 = 2 } ir_dtype;
 typedef enum {
   IR_ALGO_AUTO = 0,          /* tuned choice for (dtype, k) */
   IR_ALGO_DENSE3 = 1,        /* k = 3 only: median for every pixel with shared column sorts, packed 16x2 */
-  IR_ALGO_NETWORK = 2,       /* k <= 9: flagged pixels compacted, register selection network each */
+  IR_ALGO_NETWORK = 2,       /* k <= 7: flagged pixels compacted, register selection network each */
   IR_ALGO_BITPLANE = 3       /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
 } ir_algo;
 
@@ -124,6 +124,23 @@ ir_status ir_batch_plan_launch(ir_batch_plan *plan, void *cuda_stream);
 /* Number of kernel launches one replay of the plan performs. */
 int ir_batch_plan_kernel_count(const ir_batch_plan *plan);
 void ir_batch_plan_destroy(ir_batch_plan *plan);
+
+/* In-place filtering that allocates nothing (no handle, no cudaMalloc, no
+ * cudaFree, no allocating library call). The paper has no counterpart: this
+ * is a deployment entry point for callers that cannot allocate device memory,
+ * e.g. code inside a graph capture or a real-time frame loop, plug-ins whose
+ * host application owns all device memory, or pipelines with a fixed memory
+ * budget. Same arguments and result as ir_filter_run, with the library's
+ * default (untuned) configuration. The input copy is staged in a fixed 8 MiB
+ * device array inside the library (every GPU that loads the library holds it
+ * until exit): a frame needing more than 8 MiB (H rows of W * bytes per pixel,
+ * each row rounded up to 16 bytes) is rejected with IR_EINVAL. All calls
+ * share that array, so calls that overlap on the GPU race; order them on one
+ * stream. The first call on each device does a one-time set-up and should be
+ * made before any stream capture. Errors: IR_EINVAL (arguments, size),
+ * IR_ECUDA (launch). Device-side wait timeouts are not reported here. */
+ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pitch_bytes, ir_dtype dtype, int k,
+                                void *cuda_stream);
 
 /* Read and clear the handle's device status word (synchronises the device).
  * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call. */

@@ -27,6 +27,7 @@ EXPORTED = (
     "ir_batch_plan_create", "ir_batch_plan_launch", "ir_batch_plan_kernel_count", "ir_batch_plan_destroy",
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
+    "ir_filter_run_noalloc",
 )
 
 
@@ -84,6 +85,7 @@ def load(path: Optional[str] = None):
             "ir_status_string": ([i32], ctypes.c_char_p),
             "ir_filter_last_error": ([vp], ctypes.c_char_p),
             "ir_filter_version": ([], ctypes.c_char_p),
+            "ir_filter_run_noalloc": ([vp, i32, i32, sz, i32, i32, vp], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
