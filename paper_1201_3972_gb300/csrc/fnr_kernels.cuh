@@ -118,15 +118,43 @@ constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 cl
 // ---------------------------------------------------------------------------
 // Tile bookkeeping.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ const FrameDev *frame_of(const FnrParams &p, int t) {
-  if (p.table == nullptr) return &p.single;
-  int lo = 0, hi = p.nframes - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (p.table[mid].tile_begin <= t) lo = mid;
-    else hi = mid - 1;
+// Where the tiles of one launch come from. Frames are contiguous ranges of
+// the launch's tile index space (tile_begin); a tile is (frame, tile in frame).
+struct TileInfo {
+  int valid, f, tl, W, H, tiles_x, flags, pad;
+};
+
+__device__ __forceinline__ const FrameDev *frame_ptr(const FnrParams &p, int f) {
+  return p.table == nullptr ? &p.single : p.table + f;
+}
+
+// Thread 0 resolves tile t; `dir` is the shared-memory copy of every frame's
+// tile_begin when the launch has at most kDirMax frames (else the table is
+// searched in global memory).
+__device__ __forceinline__ TileInfo locate_tile(const FnrParams &p, const int *dir, int t) {
+  TileInfo ti{};
+  if (t >= p.total_tiles) return ti;
+  int f = 0;
+  if (p.table != nullptr) {
+    int lo = 0, hi = p.nframes - 1;
+    const bool in_smem = p.nframes <= kDirMax;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      const int tb = in_smem ? dir[mid] : p.table[mid].tile_begin;
+      if (tb <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    f = lo;
   }
-  return &p.table[lo];
+  const FrameDev *fd = frame_ptr(p, f);
+  ti.valid = 1;
+  ti.f = f;
+  ti.tl = t - fd->tile_begin;
+  ti.W = fd->W;
+  ti.H = fd->H;
+  ti.tiles_x = fd->tiles_x;
+  ti.flags = fd->flags;
+  return ti;
 }
 
 template <typename T>
@@ -149,24 +177,38 @@ __device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW,
 }
 
 // TMA fills out-of-frame cells with zero; overwrite them with the nearest
-// in-frame row, then column (replicate border).
+// in-frame row, then column (replicate border). Only out-of-frame cells are
+// touched: whole rows move as 16-byte chunks, columns one thread per row.
 template <typename T>
 __device__ void fixup_border(T *S, int xs, int ys, int BW, int BH, int W, int H) {
-  if (ys < 0 || ys + BH > H) {
-    const int top = -ys, bot = H - 1 - ys;
-    for (int i = threadIdx.x; i < BW * BH; i += kThreads) {
-      const int row = i / BW, col = i - row * BW;
-      const int src = row < top ? top : (row > bot ? bot : row);
-      if (src != row) S[i] = S[src * BW + col];
+  const int top = -ys;         // rows [0, top) lie above the frame
+  const int bot = H - 1 - ys;  // rows (bot, BH) lie below it
+  const int ntop = top > 0 ? top : 0;
+  const int nbot = bot < BH - 1 ? BH - 1 - bot : 0;
+  if (ntop + nbot > 0) {
+    const int chunks = BW * static_cast<int>(sizeof(T)) / 16;
+    const int items = (ntop + nbot) * chunks;
+    for (int i = threadIdx.x; i < items; i += kThreads) {
+      const int rr = i / chunks, c = i - rr * chunks;
+      const int row = rr < ntop ? rr : bot + 1 + (rr - ntop);
+      const int src = rr < ntop ? top : bot;
+      reinterpret_cast<uint4 *>(S + row * BW)[c] = reinterpret_cast<const uint4 *>(S + src * BW)[c];
     }
     __syncthreads();
   }
-  if (xs < 0 || xs + BW > W) {
-    const int lft = -xs, rgt = W - 1 - xs;
-    for (int i = threadIdx.x; i < BW * BH; i += kThreads) {
-      const int row = i / BW, col = i - row * BW;
-      const int src = col < lft ? lft : (col > rgt ? rgt : col);
-      if (src != col) S[i] = S[row * BW + src];
+  const int lft = -xs;         // columns [0, lft) lie left of the frame
+  const int rgt = W - 1 - xs;  // columns (rgt, BW) lie right of it
+  if (lft > 0 || rgt < BW - 1) {
+    for (int row = threadIdx.x; row < BH; row += kThreads) {
+      T *R = S + row * BW;
+      if (lft > 0) {
+        const T v = R[lft];
+        for (int j = 0; j < lft; ++j) R[j] = v;
+      }
+      if (rgt < BW - 1) {
+        const T v = R[rgt];
+        for (int j = rgt + 1; j < BW; ++j) R[j] = v;
+      }
     }
     __syncthreads();
   }
@@ -249,7 +291,7 @@ __device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint3
 
 // tw_valid, th_valid: the part of the tile inside the frame (only those
 // pixels are counted as flagged; the rest is never stored).
-template <typename T>
+template <typename T, bool COUNT>
 __device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int tw_valid, int th_valid, int &flagged) {
   constexpr int XOFF = xoff_for(1, sizeof(T));
   const int segs = TW >> 3;
@@ -295,9 +337,12 @@ __device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int tw_val
         const uint32_t sig = signal_bits(c, gmin, gmax);
         const uint32_t keep = sig * 0xffffu;
         res[pp] = (c & keep) | (gm & ~keep);
-        const int col = tx + 2 * pp;
-        const uint32_t valid = (ty + o < th_valid) ? ((col < tw_valid ? 1u : 0u) | (col + 1 < tw_valid ? 0x10000u : 0u)) : 0u;
-        flagged += __popc((sig ^ 0x00010001u) & valid);
+        if constexpr (COUNT) {
+          const int col = tx + 2 * pp;
+          const uint32_t valid =
+              (ty + o < th_valid) ? ((col < tw_valid ? 1u : 0u) | (col + 1 < tw_valid ? 0x10000u : 0u)) : 0u;
+          flagged += __popc((sig ^ 0x00010001u) & valid);
+        }
       }
       store_row8<T>(O + (ty + o) * TW + tx, res);
     }
@@ -526,8 +571,12 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
   T *const out1 = reinterpret_cast<T *>(smem + L.off_out[1]);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.off_bar);
   unsigned *misc = reinterpret_cast<unsigned *>(smem + L.off_misc);  // [0] flagged count, [1] tile OR
+  TileInfo *info = reinterpret_cast<TileInfo *>(smem + L.off_info);  // [stage]: tile staged there
+  int *dir = reinterpret_cast<int *>(smem + L.off_dir);
   const int tid = threadIdx.x;
 
+  if (p.table != nullptr && p.nframes <= kDirMax)
+    for (int f = tid; f < p.nframes; f += kThreads) dir[f] = p.table[f].tile_begin;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -536,42 +585,49 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
   }
   __syncthreads();
 
-  int t = blockIdx.x;
-  if (t >= p.total_tiles) return;
-  const FrameDev *cf = frame_of(p, t);
-  int ct = t - cf->tile_begin;
-
-  auto issue = [&](const FrameDev *f, int tl, T *dst, uint64_t *b) {
-    const int gx = (tl % f->tiles_x) * TW - XOFF;
-    const int gy = (tl / f->tiles_x) * TH - R;
+  auto issue = [&](const TileInfo &ti, T *dst, uint64_t *b) {
+    const int gx = (ti.tl % ti.tiles_x) * TW - XOFF;
+    const int gy = (ti.tl / ti.tiles_x) * TH - R;
     mbar_arrive_expect_tx(b, box_bytes);
-    tma_load_2d(dst, &f->tin, b, gx, gy);
+    tma_load_2d(dst, &frame_ptr(p, ti.f)->tin, b, gx, gy);
   };
 
-  if (tid == 0 && (cf->flags & kFrameTmaIn)) issue(cf, ct, stage0, &bar[0]);
-  uint32_t phase = 0;
+  if (tid == 0) {
+    const TileInfo first = locate_tile(p, dir, blockIdx.x);
+    info[0] = first;
+    if (first.valid && (first.flags & kFrameTmaIn)) issue(first, stage0, &bar[0]);
+  }
+  __syncthreads();
 
-  for (int i = 0;; ++i) {
+  uint32_t phase = 0;
+  int t = blockIdx.x;
+  for (int i = 0;; ++i, t += static_cast<int>(gridDim.x)) {
     const int s = i & 1;
-    const int tn = t + static_cast<int>(gridDim.x);
-    const bool has_next = tn < p.total_tiles;
-    const FrameDev *nf = has_next ? frame_of(p, tn) : nullptr;
-    const int nt = has_next ? tn - nf->tile_begin : 0;
-    const bool next_tma = has_next && (nf->flags & kFrameTmaIn);
-    if (tid == 0 && next_tma) {
-      fence_proxy_async_smem();
-      issue(nf, nt, s ? stage0 : stage1, &bar[s ^ 1]);
+    const TileInfo cur = info[s];
+    if (!cur.valid) break;
+    const FrameDev *cf = frame_ptr(p, cur.f);
+    if (tid == 0) {
+      // resolve and prefetch the next tile into the other stage (its previous
+      // tile finished with the barrier that ended the last iteration)
+      const TileInfo nx = locate_tile(p, dir, t + static_cast<int>(gridDim.x));
+      info[s ^ 1] = nx;
+      if (nx.valid && (nx.flags & kFrameTmaIn)) {
+        fence_proxy_async_smem();
+        issue(nx, s ? stage0 : stage1, &bar[s ^ 1]);
+      }
+      misc[0] = 0;
+      misc[1] = 0;
+      bulk_wait_read<1>();  // the store that last read this output buffer (two tiles ago) is done
     }
 
-    const int tile_x = ct % cf->tiles_x, tile_y = ct / cf->tiles_x;
-    const int x0 = tile_x * TW, y0 = tile_y * TH;
+    const int x0 = (cur.tl % cur.tiles_x) * TW, y0 = (cur.tl / cur.tiles_x) * TH;
     const int xs = x0 - XOFF, ys = y0 - R;
-    const bool tma_in = (cf->flags & kFrameTmaIn) != 0;
+    const bool tma_in = (cur.flags & kFrameTmaIn) != 0;
     // A TMA store clips the box at the frame edge in whole 16-byte units, so a
     // right-edge tile of a frame whose row is not a multiple of 16 bytes would
     // touch the bytes between W and the pitch: such tiles use plain stores.
-    const bool ragged_right = x0 + TW > cf->W && ((cf->W * E) & 15) != 0;
-    const bool tma_out = (cf->flags & kFrameTmaOut) != 0 && !ragged_right;
+    const bool ragged_right = x0 + TW > cur.W && ((cur.W * E) & 15) != 0;
+    const bool tma_out = (cur.flags & kFrameTmaOut) != 0 && !ragged_right;
     T *const S = s ? stage1 : stage0;
     T *const O = s ? out1 : out0;
 
@@ -582,26 +638,26 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
     } else {
       plain_tile_load<T>(cf, xs, ys, S, BW, BH);
     }
-    if (tid == 0) {
-      misc[0] = 0;
-      misc[1] = 0;
-      bulk_wait_read<1>();  // the store that last read outb[s] (two tiles ago) is done
-    }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(p.status, kStatusTimeout);
-        if (next_tma) mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u, kWaitCycles);
+        const TileInfo nx = info[s ^ 1];
+        if (nx.valid && (nx.flags & kFrameTmaIn))
+          mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u, kWaitCycles);
       }
       break;
     }
-    if (tma_in) fixup_border<T>(S, xs, ys, BW, BH, cf->W, cf->H);
+    if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
+      fixup_border<T>(S, xs, ys, BW, BH, cur.W, cur.H);
 
     if constexpr (ALGO == ALGO_DENSE3) {
       int flagged = 0;
-      dense3_tile<T>(S, O, TW, TH, BW, cf->W - x0, cf->H - y0, flagged);
       if (cf->flagged != nullptr) {
+        dense3_tile<T, true>(S, O, TW, TH, BW, cur.W - x0, cur.H - y0, flagged);
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if ((tid & 31) == 0 && flagged) atomicAdd(&misc[0], static_cast<unsigned>(flagged));
+      } else {
+        dense3_tile<T, false>(S, O, TW, TH, BW, cur.W - x0, cur.H - y0, flagged);
       }
     } else {
       uint16_t *list = reinterpret_cast<uint16_t *>(smem + L.off_list);
@@ -612,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
       }
       vertical_pass<T, K>(S, vmin, vmax, TW, TH, BW, L.vw);
       __syncthreads();
-      horizontal_flag_pass<T, K>(S, vmin, vmax, O, list, &misc[0], TW, TH, BW, L.vw, cf->W - x0, cf->H - y0);
+      horizontal_flag_pass<T, K>(S, vmin, vmax, O, list, &misc[0], TW, TH, BW, L.vw, cur.W - x0, cur.H - y0);
       __syncthreads();
       const int F = static_cast<int>(misc[0]);
       if constexpr (ALGO == ALGO_NETWORK) {
@@ -635,14 +691,13 @@ __global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant_
     }
     if (tid == 0) {
       bulk_commit();
-      if (cf->flagged != nullptr && misc[0] != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(misc[0]));
+      if (misc[0] != 0) {
+        unsigned long long *ctr = cf->flagged;
+        if (ctr != nullptr) atomicAdd(ctr, static_cast<unsigned long long>(misc[0]));
+      }
     }
     fence_proxy_async_smem();  // generic writes to this stage precede the TMA that will refill it
     __syncthreads();
-    if (!has_next) break;
-    t = tn;
-    cf = nf;
-    ct = nt;
   }
   if (tid == 0) bulk_wait_all<0>();
 }

@@ -10,6 +10,7 @@ namespace fnr {
 constexpr int kThreads = 256;          // threads per CTA for every kernel
 constexpr int kMaxK = 21;              // largest window built
 constexpr int kNumK = (kMaxK - 3) / 2 + 1;
+constexpr int kDirMax = 512;           // frames whose tile ranges a CTA keeps in shared memory
 
 enum Algo : int { ALGO_AUTO = 0, ALGO_DENSE3 = 1, ALGO_NETWORK = 2, ALGO_BITPLANE = 3 };
 
@@ -63,6 +64,8 @@ struct Layout {
   int off_planes;
   int off_bar;
   int off_misc;
+  int off_info;
+  int off_dir;
   int total;
 };
 
@@ -93,6 +96,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   }
   L.off_bar = off; off += 16;
   L.off_misc = off; off += 16;
+  L.off_info = off; off += 64;
+  L.off_dir = off; off += kDirMax * 4;
   L.total = align_up(off, 128);
   return L;
 }
