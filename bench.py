@@ -275,6 +275,8 @@ def own_arm(args):
         "gpu_launches": int(gpu_launches), "launches_per_step": launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
+    if rank == 0 and args.serve_seconds > 0:
+        result["serve"] = serve_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"], result["parity"] = cpu_baseline(frames, specs, d_out, fpx, args)
     if rank == 0:
@@ -284,6 +286,29 @@ def own_arm(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def serve_leg(args, device):
+    """64 simulated 30 fps streams (320x240 / 640x512 / 1280x1024, 14-bit,
+    10% impulses, windows 3/5/7) served by the continuous-batching server:
+    open-loop latency, closed-loop saturation throughput, and the plain
+    one-frame-per-launch path on the same traffic."""
+    from paper_1201_3972_gb300 import serve, synth
+    streams = synth.workload_serve(streams=64, pool=args.serve_pool)
+    pools = serve.make_pools(streams)
+    ref = serve.reference_hashes(pools, streams, device)
+    live = serve.simulate(streams, args.serve_seconds, pools, ref, verify_every=8, device=device)
+    sat = serve.simulate(streams, min(3.0, args.serve_seconds), pools, ref, verify_every=16, device=device,
+                         closed_loop=True)
+    plain = serve.plain_throughput(pools, streams, 64 * 12, device)
+    return {"streams": 64, "fps_per_stream": 30, "seconds": live["duration_s"],
+            "latency_ms": live["latency_ms"], "mpx_s": live["mpx_s"],
+            "frames": live["frames_completed"], "dropped": live["frames_dropped_busy"],
+            "mean_batch_frames": live["mean_batch_frames"], "max_inflight_batches": live["max_inflight_batches"],
+            "verified": live["verified"] + sat["verified"], "mismatches": live["mismatches"] + sat["mismatches"],
+            "saturation_mpx_s": sat["mpx_s"], "saturation_p99_ms": sat["latency_ms"]["p99"],
+            "plain_per_frame_mpx_s": round(plain, 1),
+            "workload": "64 streams x 30 fps Poisson, 320x240/640x512/1280x1024 u14, k 3/5/7, 10% impulses"}
 
 
 def cpu_baseline(frames, specs, d_out, fpx, args):
@@ -359,6 +384,8 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
+    ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

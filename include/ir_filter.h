@@ -157,6 +157,83 @@ ir_status ir_filter_set_config(ir_filter *h, ir_dtype dtype, int k, const ir_ker
  * each kernel node). */
 unsigned long long ir_filter_launch_count(const ir_filter *h);
 
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of frames from many video streams.
+ *
+ * A server owns its own handle on `device`, device-resident buffers per open
+ * stream (a ring of `ring_depth` input/output slots, admitted against free
+ * HBM), and two host threads: a batcher that takes every queued request
+ * (up to max_batch) as soon as one of `exec_streams` execution lanes is free,
+ * copies the frames host->device and launches one persistent kernel per
+ * (pixel type, k) class on that lane; and a completion poller that
+ * timestamps finished batches. Requests that arrive while earlier batches
+ * run join the next batch on another lane, so their work overlaps on the
+ * device. Results stay in the stream's device slot until released.
+ * The paper's claim this serves: real-time video processing (Sec. 5).
+ * ---------------------------------------------------------------------- */
+typedef struct ir_server ir_server;
+
+typedef struct {
+  int max_streams;           /* default 256 */
+  int ring_depth;            /* slots per stream, default 8 */
+  int max_batch;             /* frames per batch launch, default 256 */
+  int exec_streams;          /* batches in flight at once, default 3 */
+  size_t hbm_reserve_bytes;  /* free device memory admission leaves untouched, default 1 GiB */
+  int poll_us;               /* completion poll period in microseconds, default 20 */
+} ir_server_config;
+
+typedef struct {
+  int stream_id;
+  int slot;
+  unsigned long long tag;
+  double t_submit;           /* ir_server_clock() seconds at ir_server_submit */
+  double t_launch;           /* when its batch was launched */
+  double t_done;             /* when the batch's completion was observed */
+  int batch_frames;          /* frames in the batch it ran in */
+  int status;                /* ir_status of the batch */
+} ir_completion;
+
+typedef struct {
+  unsigned long long submitted, completed, rejected_busy, batches, frames_in_batches;
+  int open_streams;
+  int max_inflight;          /* most batches seen in flight at once */
+  size_t device_bytes;       /* device memory held for stream buffers */
+} ir_server_stats;
+
+/* cfg may be NULL (defaults). */
+ir_status ir_server_create(int device, const ir_server_config *cfg, ir_server **out);
+/* Waits for in-flight batches, stops the threads, frees everything (NULL-safe). */
+void ir_server_destroy(ir_server *srv);
+/* The server's handle, for ir_filter_set_config / ir_filter_autotune before
+ * the first stream is opened. Do not call it concurrently with the server. */
+ir_filter *ir_server_filter(ir_server *srv);
+/* Admit a stream of H x W frames: allocates ring_depth input and output
+ * slots; IR_ENOMEM if free device memory minus hbm_reserve_bytes cannot hold
+ * them, IR_EBUSY if max_streams are open. */
+ir_status ir_server_open_stream(ir_server *srv, int H, int W, ir_dtype dtype, int k, int *stream_id);
+/* IR_EBUSY while any of its slots is queued or running. */
+ir_status ir_server_close_stream(ir_server *srv, int stream_id);
+/* Queue one frame (host memory, row pitch host_pitch bytes; pinned memory
+ * gives an asynchronous copy). The frame is read when its batch launches and
+ * must stay valid until its completion is reported. *slot receives the slot
+ * index. IR_EBUSY when every slot of the stream is queued, running or holds
+ * an unreleased result. */
+ir_status ir_server_submit(ir_server *srv, int stream_id, const void *host_frame, size_t host_pitch,
+                           unsigned long long tag, int *slot);
+/* Copy up to max completions reported since the last poll; returns the count. */
+int ir_server_poll(ir_server *srv, ir_completion *out, int max);
+/* Block until every submitted frame has completed or timeout_s passes (IR_ETIMEOUT). */
+ir_status ir_server_wait_idle(ir_server *srv, double timeout_s);
+/* Device address and pitch of a completed slot's output. */
+ir_status ir_server_output(ir_server *srv, int stream_id, int slot, const void **dev_out, size_t *pitch);
+/* Copy a completed slot's output to host memory (synchronous). */
+ir_status ir_server_read(ir_server *srv, int stream_id, int slot, void *host_dst, size_t host_pitch);
+/* Return a completed slot to the stream's free pool. */
+ir_status ir_server_release(ir_server *srv, int stream_id, int slot);
+ir_status ir_server_get_stats(ir_server *srv, ir_server_stats *out);
+/* Seconds on the monotonic clock the server stamps requests with. */
+double ir_server_clock(void);
+
 const char *ir_status_string(ir_status s);
 /* Last error message of this handle ("" if none). NULL handle: last global error. */
 const char *ir_filter_last_error(const ir_filter *h);

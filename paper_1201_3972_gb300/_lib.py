@@ -28,6 +28,9 @@ EXPORTED = (
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
     "ir_filter_run_noalloc",
+    "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
+    "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
+    "ir_server_release", "ir_server_get_stats", "ir_server_clock",
 )
 
 
@@ -46,6 +49,24 @@ class ir_frame_desc(ctypes.Structure):
     _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("in_pitch", ctypes.c_size_t), ("out_pitch", ctypes.c_size_t), ("dtype", ctypes.c_int),
                 ("k", ctypes.c_int), ("flagged_count", ctypes.c_void_p)]
+
+
+class ir_server_config(ctypes.Structure):
+    _fields_ = [("max_streams", ctypes.c_int), ("ring_depth", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("exec_streams", ctypes.c_int), ("hbm_reserve_bytes", ctypes.c_size_t), ("poll_us", ctypes.c_int)]
+
+
+class ir_completion(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int), ("slot", ctypes.c_int), ("tag", ctypes.c_ulonglong),
+                ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("batch_frames", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class ir_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong),
+                ("rejected_busy", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
+                ("frames_in_batches", ctypes.c_ulonglong), ("open_streams", ctypes.c_int),
+                ("max_inflight", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
 
 
 _lock = threading.Lock()
@@ -86,6 +107,19 @@ def load(path: Optional[str] = None):
             "ir_filter_last_error": ([vp], ctypes.c_char_p),
             "ir_filter_version": ([], ctypes.c_char_p),
             "ir_filter_run_noalloc": ([vp, i32, i32, sz, i32, i32, vp], i32),
+            "ir_server_create": ([i32, ctypes.POINTER(ir_server_config), ctypes.POINTER(vp)], i32),
+            "ir_server_destroy": ([vp], None),
+            "ir_server_filter": ([vp], vp),
+            "ir_server_open_stream": ([vp, i32, i32, i32, i32, ctypes.POINTER(i32)], i32),
+            "ir_server_close_stream": ([vp, i32], i32),
+            "ir_server_submit": ([vp, i32, vp, sz, ctypes.c_ulonglong, ctypes.POINTER(i32)], i32),
+            "ir_server_poll": ([vp, ctypes.POINTER(ir_completion), i32], i32),
+            "ir_server_wait_idle": ([vp, ctypes.c_double], i32),
+            "ir_server_output": ([vp, i32, i32, ctypes.POINTER(vp), ctypes.POINTER(sz)], i32),
+            "ir_server_read": ([vp, i32, i32, vp, sz], i32),
+            "ir_server_release": ([vp, i32, i32], i32),
+            "ir_server_get_stats": ([vp, ctypes.POINTER(ir_server_stats)], i32),
+            "ir_server_clock": ([], ctypes.c_double),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -465,22 +465,33 @@ __device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uin
   }
 }
 
-// Flagged pixels: gather the k x k window into registers and run the
-// selection network.
+struct PackedOp {
+  __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) const { return vmin2(a, b); }
+  __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) const { return vmax2(a, b); }
+};
+
+// Flagged pixels, two per thread: the two k x k windows are gathered into the
+// low and high 16-bit lanes of the same registers and one packed selection
+// network serves both (an odd tail pixel is paired with itself).
 template <typename T, int K>
 __device__ void network_medians(const T *S, T *O, const uint16_t *list, int F, int TW, int BW) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
-  for (int i = threadIdx.x; i < F; i += kThreads) {
-    const int e = list[i];
-    const int ty = e >> 8, tx = e & 255;
-    const T *base = S + ty * BW + (XOFF - R) + tx;
+  const int pairs = (F + 1) >> 1;
+  for (int i = threadIdx.x; i < pairs; i += kThreads) {
+    const int ea = list[2 * i];
+    const int eb = 2 * i + 1 < F ? list[2 * i + 1] : ea;
+    const T *ba = S + (ea >> 8) * BW + (XOFF - R) + (ea & 255);
+    const T *bb = S + (eb >> 8) * BW + (XOFF - R) + (eb & 255);
     uint32_t v[K * K];
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
-      for (int b = 0; b < K; ++b) v[a * K + b] = base[a * BW + b];
-    O[ty * TW + tx] = static_cast<T>(MedianNet<K>::run(v, ScalarOp{}));
+      for (int b = 0; b < K; ++b)
+        v[a * K + b] = static_cast<uint32_t>(ba[a * BW + b]) | (static_cast<uint32_t>(bb[a * BW + b]) << 16);
+    const uint32_t m = MedianNet<K>::run(v, PackedOp{});
+    O[(ea >> 8) * TW + (ea & 255)] = static_cast<T>(m & 0xffffu);
+    O[(eb >> 8) * TW + (eb & 255)] = static_cast<T>(m >> 16);
   }
 }
 
@@ -554,7 +565,7 @@ __device__ void bitplane_medians(const uint32_t *planes, uint16_t *O16, uint8_t 
 // The kernel.
 // ---------------------------------------------------------------------------
 template <typename T, int K, int ALGO>
-__global__ void __launch_bounds__(kThreads, 2) fnr_kernel(const __grid_constant__ FnrParams p) {
+__global__ void __launch_bounds__(kThreads, (ALGO == ALGO_NETWORK ? 3 : 2)) fnr_kernel(const __grid_constant__ FnrParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int E = sizeof(T);
   constexpr int R = (K - 1) / 2;

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "fnr_host.h"
 #include "fnr_params.h"
 
 namespace fnr {
@@ -72,14 +73,6 @@ struct ir_filter {
   std::vector<PlanKey> plan_order;                        // LRU, oldest first
 };
 
-struct ClassLaunch {
-  int esize = 0, k = 0;
-  ir_kernel_config cfg{};
-  const void *fn = nullptr;
-  int grid = 0, smem = 0;
-  FnrParams prm{};
-};
-
 struct ir_batch_plan {
   ir_filter *h = nullptr;
   FrameDev *d_table = nullptr;
@@ -91,7 +84,7 @@ struct ir_batch_plan {
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
-static ir_status fail(ir_filter *h, ir_status s, const char *fmt, ...) {
+ir_status fnr::host_fail(ir_filter *h, ir_status s, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -100,6 +93,16 @@ static ir_status fail(ir_filter *h, ir_status s, const char *fmt, ...) {
   g_last_error = buf;
   if (h) h->last_error = buf;
   return s;
+}
+
+static ir_status fail(ir_filter *h, ir_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+static ir_status fail(ir_filter *h, ir_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return fnr::host_fail(h, s, "%s", buf);
 }
 
 #define IR_CUDA(h, call)                                                                     \
@@ -130,14 +133,16 @@ class DeviceGuard {
 static ir_kernel_config default_config(int esize, int k) {
   ir_kernel_config c{};
   c.ctas_per_sm = 0;
+  // measured on GB300 over the 640x512 14-bit sweep (tile sweep of all
+  // strategies): larger tiles amortise the per-tile barriers and bookkeeping
   if (k == 3) {
     c.algo = IR_ALGO_DENSE3;
     c.tile_w = 128;
-    c.tile_h = 32;
+    c.tile_h = 64;
   } else if (k <= 7) {
     c.algo = IR_ALGO_NETWORK;
     c.tile_w = 64;
-    c.tile_h = 32;
+    c.tile_h = 64;
   } else {
     c.algo = IR_ALGO_BITPLANE;
     c.tile_w = 64;
@@ -206,7 +211,7 @@ static bool encode_map(ir_filter *h, CUtensorMap *map, int esize, const void *ba
   return r == CUDA_SUCCESS;
 }
 
-static void make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t in_pitch, void *out, size_t out_pitch,
+void fnr::host_make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t in_pitch, void *out, size_t out_pitch,
                            int H, int W, int esize, int k, const ir_kernel_config &c, unsigned long long *flagged) {
   std::memset(&f, 0, sizeof f);
   const int r = (k - 1) / 2;
@@ -233,7 +238,13 @@ static void make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t in_
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-static ir_status prepare_class(ir_filter *h, ClassLaunch &cl) {
+ir_kernel_config fnr::host_config(const ir_filter *h, int esize, int k) { return h->cfg[esize - 1][kslot(k)]; }
+int fnr::host_device(const ir_filter *h) { return h->device; }
+int fnr::host_sm_count(const ir_filter *h) { return h->sm_count; }
+unsigned *fnr::host_status_word(const ir_filter *h) { return h->d_status; }
+unsigned long long *fnr::host_launch_counter(const ir_filter *h) { return h->d_launches; }
+
+ir_status fnr::host_prepare_class(ir_filter *h, ClassLaunch &cl) {
   cl.fn = get_kernel(cl.esize, cl.k, cl.cfg.algo);
   if (!cl.fn) return fail(h, IR_EUNSUPPORTED, "no kernel built for esize=%d k=%d algo=%d", cl.esize, cl.k, cl.cfg.algo);
   const Layout L = make_layout(cl.esize, cl.k, cl.cfg.algo, cl.cfg.tile_h, cl.cfg.tile_w);
@@ -258,7 +269,7 @@ static ir_status prepare_class(ir_filter *h, ClassLaunch &cl) {
   return IR_OK;
 }
 
-static ir_status launch_class(ir_filter *h, ClassLaunch &cl, cudaStream_t st) {
+ir_status fnr::host_launch_class(ir_filter *h, ClassLaunch &cl, cudaStream_t st) {
   void *args[] = {&cl.prm};
   IR_CUDA(h, cudaLaunchKernel(cl.fn, dim3(cl.grid), dim3(kThreads), args, cl.smem, st));
   return IR_OK;
@@ -288,7 +299,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.k = k;
   cl.cfg = h->cfg[cl.esize - 1][kslot(k)];
   std::memset(&cl.prm, 0, sizeof cl.prm);
-  make_frame_dev(h, cl.prm.single, in, in_pitch, out, out_pitch, H, W, cl.esize, k, cl.cfg, flagged);
+  host_make_frame_dev(h, cl.prm.single, in, in_pitch, out, out_pitch, H, W, cl.esize, k, cl.cfg, flagged);
   cl.prm.table = nullptr;
   cl.prm.nframes = 1;
   cl.prm.total_tiles = cl.prm.single.tiles_x * cl.prm.single.tiles_y;
@@ -296,10 +307,10 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.prm.tile_h = cl.cfg.tile_h;
   cl.prm.status = h->d_status;
   cl.prm.launches = h->d_launches;
-  ir_status s = prepare_class(h, cl);
+  ir_status s = host_prepare_class(h, cl);
   if (s != IR_OK) return s;
   if (flagged) IR_CUDA(h, cudaMemsetAsync(flagged, 0, sizeof(unsigned long long), st));
-  return launch_class(h, cl, st);
+  return host_launch_class(h, cl, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -480,7 +491,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     const int first = slot;
     for (int i : kv.second) {
       const ir_frame_desc &d = descs[i];
-      make_frame_dev(h, host[slot], d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, cl.esize, cl.k, cl.cfg,
+      host_make_frame_dev(h, host[slot], d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, cl.esize, cl.k, cl.cfg,
                      d.flagged_count);
       host[slot].tile_begin = tiles;
       tiles += host[slot].tiles_x * host[slot].tiles_y;
@@ -493,7 +504,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     cl.prm.tile_h = cl.cfg.tile_h;
     cl.prm.status = h->d_status;
     cl.prm.launches = h->d_launches;
-    ir_status s = prepare_class(h, cl);
+    ir_status s = host_prepare_class(h, cl);
     if (s != IR_OK) return s;
     plan->classes.push_back(cl);
     ranges.emplace_back(first, cl.prm.nframes);

@@ -91,7 +91,7 @@ const void *kernel_for_k(int esize, int k, int algo) {
 void static_config(int k, int &algo, int &tw, int &th) {
   algo = k == 3 ? ALGO_DENSE3 : (k <= 7 ? ALGO_NETWORK : ALGO_BITPLANE);
   tw = k == 3 ? 128 : 64;
-  th = 32;
+  th = k <= 7 ? 64 : 32;
 }
 
 // One-time set-up of `dev` (the current device). Called under g_mu.

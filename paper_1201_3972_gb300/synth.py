@@ -211,34 +211,44 @@ def workload_batch(n: int = 256, ks: Sequence[int] = BATCH_KS, seed_cfg: int = 3
 
 
 SERVE_SIZES = ((240, 320), (512, 640), (1024, 1280))
+SERVE_KS = (3, 5, 7)
 
 
 @dataclass(frozen=True)
 class StreamSpec:
-    """One simulated video stream: fixed resolution and window, a pool of
-    pre-generated frames it loops over, Poisson arrivals at ``fps``."""
+    """One simulated video stream: fixed resolution and window, Poisson
+    arrivals at ``fps``; its j-th frame is frame (offset + j) % pool of the
+    shared pool of its resolution (see ``serve_pool``)."""
     stream_id: int
     H: int
     W: int
     k: int
     fps: float
     pool: int
-    seeds: Tuple[int, ...] = field(default_factory=tuple)
+    offset: int
+    size_index: int
 
-    def frame_spec(self, j: int) -> FrameSpec:
-        return FrameSpec(self.H, self.W, U14, self.k, self.seeds[j % self.pool], 8.0, 0.10,
-                         "sp", False, f"stream{self.stream_id}#{j % self.pool}")
+    def pool_index(self, j: int) -> int:
+        return (self.offset + j) % self.pool
+
+
+def serve_pool(size_index: int, pool: int = 30) -> List[FrameSpec]:
+    """The pool of pre-generated 14-bit frames (10% salt-and-pepper) that all
+    streams of one resolution loop over."""
+    H, W = SERVE_SIZES[size_index]
+    return [FrameSpec(H, W, U14, 3, seed_for(4, 100 * size_index + j), 8.0, 0.10, "sp", False,
+                      f"serve {W}x{H} #{j}") for j in range(pool)]
 
 
 def workload_serve(streams: int = 64, fps: float = 30.0, pool: int = 30) -> List[StreamSpec]:
-    """64 streams: resolution round-robin over 320x240/640x512/1280x1024,
-    window round-robin over 3/5/7, 14-bit, 10% salt-and-pepper."""
+    """64 streams at 30 fps: resolution round-robin over 320x240 / 640x512 /
+    1280x1024, window round-robin over 3 / 5 / 7, 14-bit, 10% impulses."""
     out = []
     for s in range(streams):
-        H, W = SERVE_SIZES[s % len(SERVE_SIZES)]
-        k = (3, 5, 7)[(s // len(SERVE_SIZES)) % 3]
-        seeds = tuple(seed_for(4, s * pool + j) for j in range(pool))
-        out.append(StreamSpec(s, H, W, k, fps, pool, seeds))
+        si = s % len(SERVE_SIZES)
+        H, W = SERVE_SIZES[si]
+        k = SERVE_KS[(s // len(SERVE_SIZES)) % len(SERVE_KS)]
+        out.append(StreamSpec(s, H, W, k, fps, pool, (7 * s) % pool, si))
     return out
 
 
