@@ -234,6 +234,24 @@ ir_status ir_server_get_stats(ir_server *srv, ir_server_stats *out);
 /* Seconds on the monotonic clock the server stamps requests with. */
 double ir_server_clock(void);
 
+/* Closed-loop load driver (benchmarking). For `seconds`, stream
+ * stream_ids[i] keeps `inflight` copies of host_frames[i] (pitch
+ * host_pitches[i]) queued or running: every completion is released and the
+ * frame resubmitted at once, all from the calling thread. plain = 0 drives the
+ * server (batched, overlapped lanes); plain = 1 sends the same traffic
+ * round-robin through the plain path instead (per frame: one host->device copy
+ * and one ir_filter_run2 launch on one CUDA stream, into the stream's first
+ * slot), with no batching. The server must have no other traffic meanwhile. */
+typedef struct {
+  unsigned long long frames;
+  double megapixels;
+  double seconds;
+  double p50_ms, p99_ms, max_ms;   /* submit -> completion (served mode only) */
+} ir_drive_result;
+ir_status ir_server_drive(ir_server *srv, const int *stream_ids, const void *const *host_frames,
+                          const size_t *host_pitches, int n, double seconds, int inflight, int plain,
+                          ir_drive_result *out);
+
 const char *ir_status_string(ir_status s);
 /* Last error message of this handle ("" if none). NULL handle: last global error. */
 const char *ir_filter_last_error(const ir_filter *h);

@@ -30,7 +30,7 @@ EXPORTED = (
     "ir_filter_run_noalloc",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
-    "ir_server_release", "ir_server_get_stats", "ir_server_clock",
+    "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
 )
 
 
@@ -67,6 +67,11 @@ class ir_server_stats(ctypes.Structure):
                 ("rejected_busy", ctypes.c_ulonglong), ("batches", ctypes.c_ulonglong),
                 ("frames_in_batches", ctypes.c_ulonglong), ("open_streams", ctypes.c_int),
                 ("max_inflight", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
+
+
+class ir_drive_result(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_ulonglong), ("megapixels", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -120,6 +125,8 @@ def load(path: Optional[str] = None):
             "ir_server_release": ([vp, i32, i32], i32),
             "ir_server_get_stats": ([vp, ctypes.POINTER(ir_server_stats)], i32),
             "ir_server_clock": ([], ctypes.c_double),
+            "ir_server_drive": ([vp, ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.POINTER(sz), i32,
+                                 ctypes.c_double, i32, i32, ctypes.POINTER(ir_drive_result)], i32),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)

@@ -595,4 +595,113 @@ ir_status ir_server_get_stats(ir_server *s, ir_server_stats *out) {
   return IR_OK;
 }
 
+ir_status ir_server_drive(ir_server *s, const int *ids, const void *const *frames, const size_t *pitches, int n,
+                          double seconds, int inflight, int plain, ir_drive_result *out) {
+  if (!s || !ids || !frames || !pitches || n < 1 || !out || inflight < 1 || seconds <= 0) return IR_EINVAL;
+  std::memset(out, 0, sizeof *out);
+  std::vector<int> H(n), W(n), es(n), k(n);
+  std::vector<ir_dtype> dt(n);
+  std::vector<unsigned char *> d_in(n), d_out(n);
+  std::vector<size_t> dpitch(n);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (int i = 0; i < n; ++i) {
+      ir_status st = stream_ok(s, ids[i]);
+      if (st != IR_OK) return st;
+      const Stream &S = s->streams[ids[i]];
+      H[i] = S.H;
+      W[i] = S.W;
+      es[i] = S.esize;
+      k[i] = S.k;
+      dt[i] = S.dtype;
+      d_in[i] = S.slots[0].d_in;
+      d_out[i] = S.slots[0].d_out;
+      dpitch[i] = S.pitch;
+    }
+  }
+  double px = 0;
+  std::vector<double> lat;
+  const double t0 = now_s();
+  if (plain) {
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(host_device(s->h));
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      cudaSetDevice(prev);
+      return host_fail(s->h, IR_ECUDA, "drive: stream set-up failed");
+    }
+    ir_status result = IR_OK;
+    // rounds of one frame per stream; at most two rounds queued on the GPU
+    for (int round = 0; now_s() - t0 < seconds && result == IR_OK; ++round) {
+      cudaEvent_t e = ev[round & 1];
+      if (round >= 2) cudaEventSynchronize(e);
+      for (int i = 0; i < n && result == IR_OK; ++i) {
+        if (cudaMemcpy2DAsync(d_in[i], dpitch[i], frames[i], pitches[i], static_cast<size_t>(W[i]) * es[i], H[i],
+                              cudaMemcpyHostToDevice, st) != cudaSuccess) {
+          cudaGetLastError();
+          result = host_fail(s->h, IR_ECUDA, "drive: copy failed");
+          break;
+        }
+        result = ir_filter_run2(s->h, d_in[i], dpitch[i], d_out[i], dpitch[i], H[i], W[i], dt[i], k[i], st, nullptr);
+        px += static_cast<double>(H[i]) * W[i];
+        out->frames++;
+      }
+      cudaEventRecord(e, st);
+    }
+    cudaStreamSynchronize(st);
+    out->seconds = now_s() - t0;
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaStreamDestroy(st);
+    cudaSetDevice(prev);
+    out->megapixels = px / 1e6;
+    return result;
+  }
+  std::vector<int> pending(n, inflight);  // submissions owed per stream
+  std::vector<ir_completion> buf(1024);
+  unsigned long long outstanding = 0;
+  for (;;) {
+    const bool running = now_s() - t0 < seconds;
+    if (running)
+      for (int i = 0; i < n; ++i)
+        while (pending[i] > 0) {
+          int slot = -1;
+          const ir_status st = ir_server_submit(s, ids[i], frames[i], pitches[i], static_cast<unsigned long long>(i), &slot);
+          if (st == IR_EBUSY) break;
+          if (st != IR_OK) return st;
+          pending[i]--;
+          outstanding++;
+        }
+    const int m = ir_server_poll(s, buf.data(), static_cast<int>(buf.size()));
+    for (int c = 0; c < m; ++c) {
+      const ir_completion &cp = buf[c];
+      const int i = static_cast<int>(cp.tag);
+      lat.push_back((cp.t_done - cp.t_submit) * 1e3);
+      px += static_cast<double>(H[i]) * W[i];
+      out->frames++;
+      outstanding--;
+      ir_server_release(s, cp.stream_id, cp.slot);
+      pending[i]++;
+    }
+    if (!running && outstanding == 0) break;
+    if (m == 0) std::this_thread::sleep_for(std::chrono::microseconds(10));
+    if (now_s() - t0 > seconds + 30.0) return host_fail(s->h, IR_ETIMEOUT, "drive: frames did not complete");
+  }
+  out->seconds = now_s() - t0;
+  out->megapixels = px / 1e6;
+  if (!lat.empty()) {
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double q) { return lat[std::min(lat.size() - 1, static_cast<size_t>(q * (lat.size() - 1) + 0.5))]; };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    out->max_ms = lat.back();
+  }
+  return IR_OK;
+}
+
 }  // extern "C"

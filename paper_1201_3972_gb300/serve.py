@@ -282,6 +282,31 @@ def simulate(streams: Sequence[synth.StreamSpec], duration_s: float, pools: Pool
     return res
 
 
+def drive(streams: Sequence[synth.StreamSpec], pools: Pools, seconds: float, inflight: int = 2, plain: bool = False,
+          device: int = 0) -> dict:
+    """Closed-loop saturation through the library's native driver
+    (``ir_server_drive``): served (batched) or plain (one launch per frame)."""
+    srv = Server(device)
+    try:
+        sids = [srv.open_stream(s.H, s.W, synth.U14, s.k) for s in streams]
+        n = len(streams)
+        ids = (ctypes.c_int * n)(*sids)
+        fr = (ctypes.c_void_p * n)(*[pools.addrs[s.size_index][s.pool_index(0)] for s in streams])
+        pt = (ctypes.c_size_t * n)(*[s.W * 2 for s in streams])
+        res = _lib.ir_drive_result()
+        srv._err(srv.lib.ir_server_drive(srv.p, ids, fr, pt, n, seconds, inflight, 1 if plain else 0,
+                                         ctypes.byref(res)))
+        st = srv.stats()
+    finally:
+        srv.close()
+    out = {"frames": res.frames, "mpx_s": round(res.megapixels / res.seconds, 1), "seconds": round(res.seconds, 3)}
+    if not plain:
+        out.update({"p50_ms": round(res.p50_ms, 3), "p99_ms": round(res.p99_ms, 3), "max_ms": round(res.max_ms, 3),
+                    "mean_batch_frames": round(st["frames_in_batches"] / max(1, st["batches"]), 2),
+                    "max_inflight_batches": st["max_inflight"]})
+    return out
+
+
 def plain_throughput(pools: Pools, streams: Sequence[synth.StreamSpec], frames: int, device: int = 0) -> float:
     """Mpx/s of the plain path on the same kind of traffic: one frame at a
     time, host->device copy from pinned memory, ir_filter_run2, stream order."""

@@ -129,3 +129,12 @@ def test_stalled_and_non_releasing_clients_do_not_block_others(pools_and_ref):
         assert srv.submit(s0, int(f.data_ptr()), 640, 2) is None
     finally:
         srv.close()
+
+
+def test_native_drive_saturates_served_and_plain(pools_and_ref):
+    streams, pools, ref = pools_and_ref
+    served = serve.drive(streams, pools, 1.0, inflight=4)
+    plain = serve.drive(streams, pools, 1.0, plain=True)
+    assert served["frames"] > 1000 and plain["frames"] > 1000
+    assert served["mean_batch_frames"] > 1.0
+    assert served["p99_ms"] > 0
