@@ -1,15 +1,18 @@
 // Device code of the FNR impulse filter (arXiv 1201.3972, Sec. 3.3-3.4).
 //
 // One persistent kernel per (pixel type, window k, selection strategy). A CTA
-// walks a strided list of output tiles; for each tile it
-//   1. stages the tile plus a k-1 pixel halo in shared memory with a 2-D TMA
-//      load (double-buffered: the next tile's load is in flight while this one
-//      is computed), or with plain clamped loads when the frame is not 16-byte
-//      aligned, and replicates the frame border into the zero-filled part;
-//   2. computes g_min and g_max of every window (Eq. 3a/3b) and flags the
-//      pixels equal to one of them (Sec. 3.3, step 2);
-//   3. replaces flagged pixels by the window median g_m (Sec. 3.4);
-//   4. writes the output tile with a TMA store (or plain stores).
+// walks a strided list of output tiles with one producer warp and eight
+// consumer warps and no block-wide barrier in the loop:
+//   * the producer resolves each tile, waits until every consumer released
+//     the staging buffer, and stages the tile plus a k-1 pixel halo with one
+//     2-D TMA load (or clamped plain loads when the frame is not 16-byte
+//     aligned); two buffers, so the next tile loads while this one computes;
+//   * each consumer warp owns a horizontal strip of tile_h/8 output rows: it
+//     replicates the frame border into the zero-filled cells it reads,
+//     computes g_min and g_max of every window (Eq. 3a/3b), flags the pixels
+//     equal to one of them (Sec. 3.3, step 2), replaces flagged pixels by the
+//     window median g_m (Sec. 3.4), writes its strip with a TMA store (or
+//     plain stores) and releases the buffer.
 // All arithmetic is integer min/max/compare, so results are bit-exact.
 #pragma once
 
@@ -39,6 +42,10 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -118,19 +125,18 @@ constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 cl
 // ---------------------------------------------------------------------------
 // Tile bookkeeping.
 // ---------------------------------------------------------------------------
-// Where the tiles of one launch come from. Frames are contiguous ranges of
-// the launch's tile index space (tile_begin); a tile is (frame, tile in frame).
+// Frames are contiguous ranges of the launch's tile index space (tile_begin);
+// a tile is (frame, tile in frame).
 struct TileInfo {
-  int valid, f, tl, W, H, tiles_x, flags, pad;
+  int valid, f, x0, y0, W, H, flags, counted;  // counted: the frame has a flagged-pixel counter
 };
 
 __device__ __forceinline__ const FrameDev *frame_ptr(const FnrParams &p, int f) {
   return p.table == nullptr ? &p.single : p.table + f;
 }
 
-// Thread 0 resolves tile t; `dir` is the shared-memory copy of every frame's
-// tile_begin when the launch has at most kDirMax frames (else the table is
-// searched in global memory).
+// `dir` is the shared-memory copy of every frame's tile_begin when the launch
+// has at most kDirMax frames (else the table is searched in global memory).
 __device__ __forceinline__ TileInfo locate_tile(const FnrParams &p, const int *dir, int t) {
   TileInfo ti{};
   if (t >= p.total_tiles) return ti;
@@ -147,13 +153,16 @@ __device__ __forceinline__ TileInfo locate_tile(const FnrParams &p, const int *d
     f = lo;
   }
   const FrameDev *fd = frame_ptr(p, f);
+  const int tl = t - fd->tile_begin;
+  const int tiles_x = fd->tiles_x;
   ti.valid = 1;
   ti.f = f;
-  ti.tl = t - fd->tile_begin;
+  ti.x0 = (tl % tiles_x) * p.tile_w;
+  ti.y0 = (tl / tiles_x) * p.tile_h;
   ti.W = fd->W;
   ti.H = fd->H;
-  ti.tiles_x = fd->tiles_x;
   ti.flags = fd->flags;
+  ti.counted = fd->flagged != nullptr;
   return ti;
 }
 
@@ -162,73 +171,76 @@ __device__ __forceinline__ T load_global(const unsigned char *base, long long pi
   return __ldg(reinterpret_cast<const T *>(base + (long long)y * pitch) + x);
 }
 
-// Plain staging for frames TMA cannot address: clamped coordinates give the
-// replicated border directly.
+// Plain staging by one warp for frames TMA cannot address: clamped
+// coordinates give the replicated border directly.
 template <typename T>
-__device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW, int BH) {
+__device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW, int BH, int lane) {
   const int H = f->H, W = f->W;
-  for (int i = threadIdx.x; i < BW * BH; i += kThreads) {
-    const int row = i / BW, col = i - row * BW;
-    int gy = ys + row, gx = xs + col;
+  for (int row = 0; row < BH; ++row) {
+    int gy = ys + row;
     gy = gy < 0 ? 0 : (gy >= H ? H - 1 : gy);
-    gx = gx < 0 ? 0 : (gx >= W ? W - 1 : gx);
-    S[i] = load_global<T>(f->in, f->in_pitch, gy, gx);
+    for (int col = lane; col < BW; col += 32) {
+      int gx = xs + col;
+      gx = gx < 0 ? 0 : (gx >= W ? W - 1 : gx);
+      S[row * BW + col] = load_global<T>(f->in, f->in_pitch, gy, gx);
+    }
   }
 }
 
-// TMA fills out-of-frame cells with zero; overwrite them with the nearest
-// in-frame row, then column (replicate border). Only out-of-frame cells are
-// touched: whole rows move as 16-byte chunks, columns one thread per row.
+// TMA fills out-of-frame cells with zero. A warp replaces, in the stage rows
+// [row0, row1) it is about to read, every out-of-frame cell by the nearest
+// in-frame one: first the in-frame columns of out-of-frame rows (copied from
+// the nearest in-frame row), then the out-of-frame columns of every row (from
+// the row's own edge cell). Several warps may patch the same cell; every
+// write stores that cell's final value, so the overlap is harmless.
 template <typename T>
-__device__ void fixup_border(T *S, int xs, int ys, int BW, int BH, int W, int H) {
-  const int top = -ys;         // rows [0, top) lie above the frame
-  const int bot = H - 1 - ys;  // rows (bot, BH) lie below it
-  const int ntop = top > 0 ? top : 0;
-  const int nbot = bot < BH - 1 ? BH - 1 - bot : 0;
-  if (ntop + nbot > 0) {
-    const int chunks = BW * static_cast<int>(sizeof(T)) / 16;
-    const int items = (ntop + nbot) * chunks;
-    for (int i = threadIdx.x; i < items; i += kThreads) {
-      const int rr = i / chunks, c = i - rr * chunks;
-      const int row = rr < ntop ? rr : bot + 1 + (rr - ntop);
-      const int src = rr < ntop ? top : bot;
-      reinterpret_cast<uint4 *>(S + row * BW)[c] = reinterpret_cast<const uint4 *>(S + src * BW)[c];
-    }
-    __syncthreads();
+__device__ void fixup_rows_warp(T *S, int xs, int ys, int BW, int W, int H, int row0, int row1, int lane) {
+  const int top = -ys, bot = H - 1 - ys;     // stage rows of frame rows 0 and H-1
+  const int lft = -xs, rgt = W - 1 - xs;     // stage columns of frame columns 0 and W-1
+  const int c0 = lft > 0 ? lft : 0;
+  const int c1 = rgt < BW - 1 ? rgt : BW - 1;
+  for (int row = row0; row < row1; ++row) {
+    const int src = row < top ? top : (row > bot ? bot : row);
+    if (src != row)
+      for (int c = c0 + lane; c <= c1; c += 32) S[row * BW + c] = S[src * BW + c];
   }
-  const int lft = -xs;         // columns [0, lft) lie left of the frame
-  const int rgt = W - 1 - xs;  // columns (rgt, BW) lie right of it
+  __syncwarp();
   if (lft > 0 || rgt < BW - 1) {
-    for (int row = threadIdx.x; row < BH; row += kThreads) {
-      T *R = S + row * BW;
+    for (int row = row0 + lane; row < row1; row += 32) {
+      T *Rw = S + row * BW;
       if (lft > 0) {
-        const T v = R[lft];
-        for (int j = 0; j < lft; ++j) R[j] = v;
+        const T v = Rw[lft];
+        for (int j = 0; j < lft; ++j) Rw[j] = v;
       }
       if (rgt < BW - 1) {
-        const T v = R[rgt];
-        for (int j = rgt + 1; j < BW; ++j) R[j] = v;
+        const T v = Rw[rgt];
+        for (int j = rgt + 1; j < BW; ++j) Rw[j] = v;
       }
     }
-    __syncthreads();
   }
+  __syncwarp();
 }
 
+// Plain store of output rows [r0, r0+rows) of the tile (frame-clipped).
 template <typename T>
-__device__ void plain_tile_store(const FrameDev *f, const T *O, int x0, int y0, int TW, int TH) {
+__device__ void plain_strip_store(const FrameDev *f, const T *O, int x0, int y0, int TW, int r0, int rows, int lane) {
   const int H = f->H, W = f->W;
-  for (int i = threadIdx.x; i < TW * TH; i += kThreads) {
-    const int row = i / TW, col = i - row * TW;
-    const int gy = y0 + row, gx = x0 + col;
-    if (gy < H && gx < W) reinterpret_cast<T *>(f->out + (long long)gy * f->out_pitch)[gx] = O[i];
+  for (int row = r0; row < r0 + rows; ++row) {
+    const int gy = y0 + row;
+    if (gy >= H) break;
+    T *dst = reinterpret_cast<T *>(f->out + (long long)gy * f->out_pitch);
+    for (int col = lane; col < TW; col += 32) {
+      const int gx = x0 + col;
+      if (gx < W) dst[gx] = O[row * TW + col];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // DENSE3: k = 3, median for every pixel.
 //
-// A thread owns 8 consecutive outputs in 2 consecutive rows. Pixels are held
-// as packed pairs (x, x+1) of 16-bit lanes. Each of the 4 input rows gives 6
+// A lane owns 8 consecutive outputs in 2 consecutive rows. Pixels are held as
+// packed pairs (x, x+1) of 16-bit lanes. Each of the 4 input rows gives 6
 // even-aligned pair words E_-1..E_4 covering columns x-2..x+9. Columns are
 // sorted vertically once (sort of the shared middle two rows, then one
 // insertion per output row), and the odd-aligned pairs (x-1,x), (x+1,x+2)...
@@ -289,16 +301,22 @@ __device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint3
   return vmin2(vmin2(c - gmin, gmax - c), 0x00010001u);
 }
 
-// tw_valid, th_valid: the part of the tile inside the frame (only those
-// pixels are counted as flagged; the rest is never stored).
+// Output rows [r0, r0+SR) of the tile, written straight to the frame: 16-byte
+// (u16) or 8-byte (u8) stores when the 8 pixels are inside the frame and the
+// frame is 16-byte aligned, else per-pixel stores clipped to the frame.
+// tw_valid, th_valid: the part of the tile inside the frame. tile_w / 8 is a
+// power of two (seg_shift = log2 of it).
 template <typename T, bool COUNT>
-__device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int tw_valid, int th_valid, int &flagged) {
+__device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int TW, int BW, int r0, int SR,
+                             int seg_shift, int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged) {
   constexpr int XOFF = xoff_for(1, sizeof(T));
-  const int segs = TW >> 3;
-  const int items = (TH >> 1) * segs;
-  for (int it = threadIdx.x; it < items; it += kThreads) {
-    const int sx = it % segs, ry = it / segs;
-    const int tx = sx << 3, ty = ry << 1;
+  const int items = (SR >> 1) << seg_shift;
+  const int seg_mask = (1 << seg_shift) - 1;
+  unsigned char *const out = f->out;
+  const long long pitch = f->out_pitch;
+  for (int it = lane; it < items; it += 32) {
+    const int sx = it & seg_mask, ry = it >> seg_shift;
+    const int tx = sx << 3, ty = r0 + (ry << 1);
     uint32_t e[4][6];
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) load_row8<T>(S + (ty + rr) * BW + XOFF + tx, e[rr]);
@@ -344,14 +362,23 @@ __device__ void dense3_tile(const T *S, T *O, int TW, int TH, int BW, int tw_val
           flagged += __popc((sig ^ 0x00010001u) & valid);
         }
       }
-      store_row8<T>(O + (ty + o) * TW + tx, res);
+      if (ty + o < th_valid) {
+        T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + tx;
+        if (vec_ok && tx + 8 <= tw_valid) {
+          store_row8<T>(dst, res);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (tx + q < tw_valid) dst[q] = static_cast<T>((res[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+        }
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Compacted strategies (any k): separable g_min/g_max, flag, list of flagged
-// pixels, then one median per flagged pixel.
+// Compacted strategies (any k): separable g_min/g_max over the warp's strip,
+// flag, warp-local list of flagged pixels, then one median per flagged pixel.
 // ---------------------------------------------------------------------------
 
 // Sliding extreme over windows [q, q+K-1], q = 0..RG-1, of RG+K-1 values,
@@ -380,21 +407,16 @@ __device__ __forceinline__ void sliding_extreme(const uint32_t (&v)[RG + K - 1],
   }
 }
 
-template <int K>
-struct RowGroup {
-  static constexpr int value = K >= 8 ? 8 : (K >= 4 ? 4 : 2);
-};
-
-// Vertical pass: vmin/vmax[ty][j] = min/max of stage column (XOFF-R+j) over
-// rows ty..ty+K-1, for ty < TH and j < TW + K - 1.
+// Vertical pass over the strip: vmin/vmax[q][j] = min/max of stage column
+// (XOFF-R+j) over stage rows r0+q .. r0+q+K-1, q < SR, j < VW.
 template <typename T, int K>
-__device__ void vertical_pass(const T *S, uint16_t *vmin, uint16_t *vmax, int TW, int TH, int BW, int VW) {
-  constexpr int R = (K - 1) / 2, RG = RowGroup<K>::value;
+__device__ void vertical_strip(const T *S, uint16_t *vmin, uint16_t *vmax, int BW, int VW, int r0, int SR, int lane) {
+  constexpr int R = (K - 1) / 2, RG = row_group(K);
   constexpr int XOFF = xoff_for(R, sizeof(T));
-  const int items = VW * (TH / RG);
-  for (int it = threadIdx.x; it < items; it += kThreads) {
-    const int j = it % VW, g = it / VW;
-    const T *col = S + g * RG * BW + (XOFF - R) + j;
+  const int items = VW * (SR / RG);
+  for (int it = lane; it < items; it += 32) {
+    const int g = it / VW, j = it - g * VW;
+    const T *col = S + (r0 + g * RG) * BW + (XOFF - R) + j;
     uint32_t v[RG + K - 1];
 #pragma unroll
     for (int i = 0; i < RG + K - 1; ++i) v[i] = col[i * BW];
@@ -409,34 +431,34 @@ __device__ void vertical_pass(const T *S, uint16_t *vmin, uint16_t *vmax, int TW
   }
 }
 
-// Horizontal pass + flag: writes every centre value to the output tile and
-// appends flagged pixels (ty << 8 | tx) to the list. Returns nothing; the
-// list length accumulates in *count.
+// Horizontal pass + flag over the strip: every centre value goes to the
+// output tile; flagged in-frame pixels are appended to the warp's list as
+// (row in strip << 8 | column). Returns the list length (warp-uniform).
 template <typename T, int K>
-__device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uint16_t *vmax, T *O,
-                                     uint16_t *list, unsigned *count, int TW, int TH, int BW, int VW, int tw_valid,
-                                     int th_valid) {
-  constexpr int R = (K - 1) / 2, RG = RowGroup<K>::value;
+__device__ int horizontal_flag_strip(const T *S, const uint16_t *vmin, const uint16_t *vmax, T *O, uint16_t *list,
+                                     int TW, int BW, int VW, int r0, int SR, int tw_valid, int th_valid, int lane) {
+  constexpr int R = (K - 1) / 2, RG = row_group(K);
   constexpr int XOFF = xoff_for(R, sizeof(T));
   const int per_row = TW / RG;
-  const int items = TH * per_row;
-  const int lane = threadIdx.x & 31;
-  for (int it0 = 0; it0 < items; it0 += kThreads) {
-    const int it = it0 + threadIdx.x;
+  const int items = SR * per_row;
+  int base = 0;
+  for (int it0 = 0; it0 < items; it0 += 32) {
+    const int it = it0 + lane;
     uint32_t fm = 0;
-    int ty = 0, tx0 = 0;
+    int q0 = 0, tx0 = 0;
     if (it < items) {
-      ty = it / per_row;
-      tx0 = (it - ty * per_row) * RG;
+      q0 = it / per_row;
+      tx0 = (it - q0 * per_row) * RG;
       uint32_t hmn[RG + K - 1], hmx[RG + K - 1];
 #pragma unroll
       for (int i = 0; i < RG + K - 1; ++i) {
-        hmn[i] = vmin[ty * VW + tx0 + i];
-        hmx[i] = vmax[ty * VW + tx0 + i];
+        hmn[i] = vmin[q0 * VW + tx0 + i];
+        hmx[i] = vmax[q0 * VW + tx0 + i];
       }
       uint32_t gmin[RG], gmax[RG];
       sliding_extreme<K, RG, false>(hmn, gmin);
       sliding_extreme<K, RG, true>(hmx, gmax);
+      const int ty = r0 + q0;
       const T *crow = S + (ty + R) * BW + XOFF + tx0;
 #pragma unroll
       for (int q = 0; q < RG; ++q) {
@@ -446,7 +468,6 @@ __device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uin
         fm |= static_cast<uint32_t>(inside && (c == gmin[q] || c == gmax[q])) << q;
       }
     }
-    // warp-aggregated append
     const int cnt = __popc(fm);
     int incl = cnt;
 #pragma unroll
@@ -454,15 +475,14 @@ __device__ void horizontal_flag_pass(const T *S, const uint16_t *vmin, const uin
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int base = 0;
-    if (lane == 31 && total) base = static_cast<int>(atomicAdd(count, static_cast<unsigned>(total)));
-    base = __shfl_sync(0xffffffffu, base, 31);
     int pos = base + incl - cnt;
 #pragma unroll
     for (int q = 0; q < RG; ++q)
-      if ((fm >> q) & 1u) list[pos++] = static_cast<uint16_t>((ty << 8) | (tx0 + q));
+      if ((fm >> q) & 1u) list[pos++] = static_cast<uint16_t>((q0 << 8) | (tx0 + q));
+    base += __shfl_sync(0xffffffffu, incl, 31);
   }
+  __syncwarp();
+  return base;
 }
 
 struct PackedOp {
@@ -470,67 +490,70 @@ struct PackedOp {
   __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) const { return vmax2(a, b); }
 };
 
-// Flagged pixels, two per thread: the two k x k windows are gathered into the
-// low and high 16-bit lanes of the same registers and one packed selection
-// network serves both (an odd tail pixel is paired with itself).
+// Flagged pixels of the strip, two per lane: the two k x k windows are
+// gathered into the low and high 16-bit lanes of the same registers and one
+// packed selection network serves both (an odd tail pixel pairs with itself).
 template <typename T, int K>
-__device__ void network_medians(const T *S, T *O, const uint16_t *list, int F, int TW, int BW) {
+__device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
   const int pairs = (F + 1) >> 1;
-  for (int i = threadIdx.x; i < pairs; i += kThreads) {
+  for (int i = lane; i < pairs; i += 32) {
     const int ea = list[2 * i];
     const int eb = 2 * i + 1 < F ? list[2 * i + 1] : ea;
-    const T *ba = S + (ea >> 8) * BW + (XOFF - R) + (ea & 255);
-    const T *bb = S + (eb >> 8) * BW + (XOFF - R) + (eb & 255);
+    const int ya = r0 + (ea >> 8), xa = ea & 255, yb = r0 + (eb >> 8), xb = eb & 255;
+    const T *ba = S + ya * BW + (XOFF - R) + xa;
+    const T *bb = S + yb * BW + (XOFF - R) + xb;
     uint32_t v[K * K];
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
       for (int b = 0; b < K; ++b)
-        v[a * K + b] = static_cast<uint32_t>(ba[a * BW + b]) | (static_cast<uint32_t>(bb[a * BW + b]) << 16);
+        v[a * K + b] = __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
     const uint32_t m = MedianNet<K>::run(v, PackedOp{});
-    O[(ea >> 8) * TW + (ea & 255)] = static_cast<T>(m & 0xffffu);
-    O[(eb >> 8) * TW + (eb & 255)] = static_cast<T>(m >> 16);
+    O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
+    O[yb * TW + xb] = static_cast<T>(m >> 16);
   }
 }
 
-// Bit planes of the staged tile: plane b, row i, word w holds bit b of the
-// 32 pixels of row i starting at column 32w. One ballot per (row, word, bit).
+// Bit planes of the stage rows [r0, r0 + rows): plane b, row i, word w holds
+// bit b of the 32 pixels of row r0+i starting at column 32w. One ballot per
+// (row, word, bit). Returns the OR of all those pixels (warp-uniform).
 template <typename T>
-__device__ void build_planes(const T *S, uint32_t *planes, unsigned *tile_or, int BW, int BH, int PW, int NBMAX) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int r0, int rows, int PW, int NBMAX,
+                                      int lane) {
   const int wpr = PW - 1;
-  const int items = BH * wpr;
   uint32_t orv = 0;
-  for (int it = warp; it < items; it += kThreads / 32) {
+  for (int it = 0; it < rows * wpr; ++it) {
     const int row = it / wpr, w = it - row * wpr;
     const int col = (w << 5) + lane;
-    const uint32_t v = col < BW ? static_cast<uint32_t>(S[row * BW + col]) : 0u;
+    const uint32_t v = col < BW ? static_cast<uint32_t>(S[(r0 + row) * BW + col]) : 0u;
     orv |= v;
     uint32_t mine = 0;
     for (int b = 0; b < NBMAX; ++b) {
       const uint32_t bits = __ballot_sync(0xffffffffu, (v >> b) & 1u);
       if (lane == b) mine = bits;
     }
-    if (lane < NBMAX) planes[(lane * BH + row) * PW + w] = mine;
+    if (lane < NBMAX) planes[(lane * rows + row) * PW + w] = mine;
   }
-  for (int it = threadIdx.x; it < NBMAX * BH; it += kThreads) planes[it * PW + wpr] = 0u;
-  orv = __reduce_or_sync(0xffffffffu, orv);
-  if (lane == 0 && orv) atomicOr(tile_or, orv);
+  for (int it = lane; it < NBMAX * rows; it += 32) planes[it * PW + wpr] = 0u;
+  __syncwarp();
+  return __reduce_or_sync(0xffffffffu, orv);
 }
 
-// Flagged pixels: radix select on the window, most significant bit first.
-// alive[a] marks the window pixels of row a whose bits above the current bit
-// match the answer so far; each round counts the live pixels with a 0 bit.
-template <int K>
-__device__ void bitplane_medians(const uint32_t *planes, uint16_t *O16, uint8_t *O8, bool is16,
-                                 const uint16_t *list, int F, int TW, int BH, int PW, int NB, int XOFF) {
+// Flagged pixels of the strip: radix select on the window, most significant
+// bit first. alive[a] marks the window pixels of row a whose bits above the
+// current bit match the answer so far; each round counts the live pixels
+// with a 0 bit. Plane rows are relative to the strip's first stage row.
+template <typename T, int K>
+__device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *list, int F, int TW, int rows, int PW,
+                               int NB, int r0, int lane) {
   constexpr int R = (K - 1) / 2;
+  constexpr int XOFF = xoff_for(R, sizeof(T));
   constexpr uint32_t kMask = (1u << K) - 1u;
-  for (int i = threadIdx.x; i < F; i += kThreads) {
+  for (int i = lane; i < F; i += 32) {
     const int e = list[i];
-    const int ty = e >> 8, tx = e & 255;
+    const int q = e >> 8, tx = e & 255;
     const int c0 = XOFF - R + tx;
     const int wi = c0 >> 5, sh = c0 & 31;
     uint32_t alive[K];
@@ -538,7 +561,7 @@ __device__ void bitplane_medians(const uint32_t *planes, uint16_t *O16, uint8_t 
     for (int a = 0; a < K; ++a) alive[a] = kMask;
     uint32_t rank = (K * K - 1) / 2, res = 0;
     for (int b = NB - 1; b >= 0; --b) {
-      const uint32_t *P = planes + (b * BH + ty) * PW + wi;
+      const uint32_t *P = planes + (b * rows + q) * PW + wi;
       uint32_t seg[K];
       uint32_t cnt = 0;
 #pragma unroll
@@ -556,16 +579,20 @@ __device__ void bitplane_medians(const uint32_t *planes, uint16_t *O16, uint8_t 
         for (int a = 0; a < K; ++a) alive[a] &= seg[a];
       }
     }
-    if (is16) O16[ty * TW + tx] = static_cast<uint16_t>(res);
-    else O8[ty * TW + tx] = static_cast<uint8_t>(res);
+    O[(r0 + q) * TW + tx] = static_cast<T>(res);
   }
 }
 
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
+template <int ALGO>
+struct MinBlocks {
+  static constexpr int value = ALGO == ALGO_BITPLANE ? 1 : 3;
+};
+
 template <typename T, int K, int ALGO>
-__global__ void __launch_bounds__(kThreads, (ALGO == ALGO_NETWORK ? 3 : 2)) fnr_kernel(const __grid_constant__ FnrParams p) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<ALGO>::value) fnr_kernel(const __grid_constant__ FnrParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int E = sizeof(T);
   constexpr int R = (K - 1) / 2;
@@ -574,64 +601,78 @@ __global__ void __launch_bounds__(kThreads, (ALGO == ALGO_NETWORK ? 3 : 2)) fnr_
 
   const int TW = p.tile_w, TH = p.tile_h;
   const Layout L = make_layout(E, K, ALGO, TH, TW);
-  const int BW = L.bw, BH = L.bh;
+  const int BW = L.bw, BH = L.bh, SR = L.sr;
   const uint32_t box_bytes = static_cast<uint32_t>(BW * BH * E);
   T *const stage0 = reinterpret_cast<T *>(smem + L.off_stage[0]);
   T *const stage1 = reinterpret_cast<T *>(smem + L.off_stage[1]);
   T *const out0 = reinterpret_cast<T *>(smem + L.off_out[0]);
   T *const out1 = reinterpret_cast<T *>(smem + L.off_out[1]);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.off_bar);
-  unsigned *misc = reinterpret_cast<unsigned *>(smem + L.off_misc);  // [0] flagged count, [1] tile OR
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bar);  // [2]: tile staged
+  uint64_t *empty = full + 2;                                        // [2]: all consumers done with it
   TileInfo *info = reinterpret_cast<TileInfo *>(smem + L.off_info);  // [stage]: tile staged there
   int *dir = reinterpret_cast<int *>(smem + L.off_dir);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (p.table != nullptr && p.nframes <= kDirMax)
     for (int f = tid; f < p.nframes; f += kThreads) dir[f] = p.table[f].tile_begin;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], kConsumerWarps);
+    mbar_init(&empty[1], kConsumerWarps);
     fence_mbar_init();
     if (blockIdx.x == 0 && p.launches != nullptr) atomicAdd(p.launches, 1ull);
   }
-  __syncthreads();
+  __syncthreads();  // the only block-wide barrier
 
-  auto issue = [&](const TileInfo &ti, T *dst, uint64_t *b) {
-    const int gx = (ti.tl % ti.tiles_x) * TW - XOFF;
-    const int gy = (ti.tl / ti.tiles_x) * TH - R;
-    mbar_arrive_expect_tx(b, box_bytes);
-    tma_load_2d(dst, &frame_ptr(p, ti.f)->tin, b, gx, gy);
-  };
-
-  if (tid == 0) {
-    const TileInfo first = locate_tile(p, dir, blockIdx.x);
-    info[0] = first;
-    if (first.valid && (first.flags & kFrameTmaIn)) issue(first, stage0, &bar[0]);
+  if (warp == kConsumerWarps) {
+    // ------------------------------------------------------------- producer
+    for (int i = 0;; ++i) {
+      const int s = i & 1;
+      if (i >= 2 && !mbar_wait_bounded(&empty[s], ((i >> 1) - 1) & 1u, kWaitCycles)) {
+        if (lane == 0) atomicOr(p.status, kStatusTimeout);
+        break;
+      }
+      const TileInfo ti = locate_tile(p, dir, blockIdx.x + i * static_cast<int>(gridDim.x));
+      T *const S = s ? stage1 : stage0;
+      if (lane == 0) info[s] = ti;
+      if (!ti.valid) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+        break;
+      }
+      const int xs = ti.x0 - XOFF;
+      const int ys = ti.y0 - R;
+      if (ti.flags & kFrameTmaIn) {
+        if (lane == 0) {
+          fence_proxy_async_smem();
+          mbar_arrive_expect_tx(&full[s], box_bytes);
+          tma_load_2d(S, &frame_ptr(p, ti.f)->tin, &full[s], xs, ys);
+        }
+      } else {
+        plain_tile_load<T>(frame_ptr(p, ti.f), xs, ys, S, BW, BH, lane);
+        fence_proxy_async_smem();  // these generic writes precede a later TMA refill of the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+      }
+    }
+    return;
   }
-  __syncthreads();
 
-  uint32_t phase = 0;
-  int t = blockIdx.x;
-  for (int i = 0;; ++i, t += static_cast<int>(gridDim.x)) {
+  // --------------------------------------------------------------- consumers
+  const int r0 = warp * SR;  // this warp's output rows [r0, r0 + SR)
+  const int seg_shift = 31 - __clz(TW >> 3);  // dense 3x3: tile_w / 8 is a power of two
+  unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;
+  for (int i = 0;; ++i) {
     const int s = i & 1;
+    if (!mbar_wait_bounded(&full[s], (i >> 1) & 1u, kWaitCycles)) {
+      if (lane == 0) atomicOr(p.status, kStatusTimeout);
+      break;
+    }
     const TileInfo cur = info[s];
     if (!cur.valid) break;
     const FrameDev *cf = frame_ptr(p, cur.f);
-    if (tid == 0) {
-      // resolve and prefetch the next tile into the other stage (its previous
-      // tile finished with the barrier that ended the last iteration)
-      const TileInfo nx = locate_tile(p, dir, t + static_cast<int>(gridDim.x));
-      info[s ^ 1] = nx;
-      if (nx.valid && (nx.flags & kFrameTmaIn)) {
-        fence_proxy_async_smem();
-        issue(nx, s ? stage0 : stage1, &bar[s ^ 1]);
-      }
-      misc[0] = 0;
-      misc[1] = 0;
-      bulk_wait_read<1>();  // the store that last read this output buffer (two tiles ago) is done
-    }
-
-    const int x0 = (cur.tl % cur.tiles_x) * TW, y0 = (cur.tl / cur.tiles_x) * TH;
+    const int x0 = cur.x0, y0 = cur.y0;
     const int xs = x0 - XOFF, ys = y0 - R;
     const bool tma_in = (cur.flags & kFrameTmaIn) != 0;
     // A TMA store clips the box at the frame edge in whole 16-byte units, so a
@@ -641,76 +682,66 @@ __global__ void __launch_bounds__(kThreads, (ALGO == ALGO_NETWORK ? 3 : 2)) fnr_
     const bool tma_out = (cur.flags & kFrameTmaOut) != 0 && !ragged_right;
     T *const S = s ? stage1 : stage0;
     T *const O = s ? out1 : out0;
+    const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
-    bool ok = true;
-    if (tma_in) {
-      ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, kWaitCycles);
-      phase ^= 1u << s;
-    } else {
-      plain_tile_load<T>(cf, xs, ys, S, BW, BH);
-    }
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(p.status, kStatusTimeout);
-        const TileInfo nx = info[s ^ 1];
-        if (nx.valid && (nx.flags & kFrameTmaIn))
-          mbar_wait_bounded(&bar[s ^ 1], (phase >> (s ^ 1)) & 1u, kWaitCycles);
-      }
-      break;
-    }
-    if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
-      fixup_border<T>(S, xs, ys, BW, BH, cur.W, cur.H);
-
-    if constexpr (ALGO == ALGO_DENSE3) {
+    if (live && ALGO == ALGO_DENSE3) {
+      if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, lane);
+      // results go straight from registers to the frame (no output tile)
+      const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
-      if (cf->flagged != nullptr) {
-        dense3_tile<T, true>(S, O, TW, TH, BW, cur.W - x0, cur.H - y0, flagged);
+      if (cur.counted) {
+        dense3_strip<T, true>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
+                              flagged);
         flagged = __reduce_add_sync(0xffffffffu, flagged);
-        if ((tid & 31) == 0 && flagged) atomicAdd(&misc[0], static_cast<unsigned>(flagged));
+        if (lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else {
-        dense3_tile<T, false>(S, O, TW, TH, BW, cur.W - x0, cur.H - y0, flagged);
+        dense3_strip<T, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
+                               flagged);
       }
-    } else {
-      uint16_t *list = reinterpret_cast<uint16_t *>(smem + L.off_list);
-      uint16_t *vmin = reinterpret_cast<uint16_t *>(smem + L.off_vmin);
-      uint16_t *vmax = reinterpret_cast<uint16_t *>(smem + L.off_vmax);
-      if constexpr (ALGO == ALGO_BITPLANE) {
-        build_planes<T>(S, reinterpret_cast<uint32_t *>(smem + L.off_planes), &misc[1], BW, BH, L.pw, L.nbmax);
+    } else if (live) {
+      if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, lane);
+      if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
+      __syncwarp();
+      int flagged = 0;
+      {
+        uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
+        uint16_t *vmin = reinterpret_cast<uint16_t *>(wbase + L.w_vmin);
+        uint16_t *vmax = reinterpret_cast<uint16_t *>(wbase + L.w_vmax);
+        vertical_strip<T, K>(S, vmin, vmax, BW, L.vw, r0, SR, lane);
+        __syncwarp();
+        flagged = horizontal_flag_strip<T, K>(S, vmin, vmax, O, list, TW, BW, L.vw, r0, SR, cur.W - x0, cur.H - y0,
+                                              lane);
+        if constexpr (ALGO == ALGO_NETWORK) {
+          network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
+        } else {
+          uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
+          const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, L.nbmax, lane);
+          bitplane_strip<T, K>(planes, O, list, flagged, TW, L.plane_rows, L.pw, 32 - __clz(static_cast<int>(orv)),
+                               r0, lane);
+        }
       }
-      vertical_pass<T, K>(S, vmin, vmax, TW, TH, BW, L.vw);
-      __syncthreads();
-      horizontal_flag_pass<T, K>(S, vmin, vmax, O, list, &misc[0], TW, TH, BW, L.vw, cur.W - x0, cur.H - y0);
-      __syncthreads();
-      const int F = static_cast<int>(misc[0]);
-      if constexpr (ALGO == ALGO_NETWORK) {
-        network_medians<T, K>(S, O, list, F, TW, BW);
+      __syncwarp();
+      if (tma_out) {
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tma_store_2d(&cf->tout, O + r0 * TW, x0, y0 + r0);
       } else {
-        const int NB = 32 - __clz(static_cast<int>(misc[1]));
-        bitplane_medians<K>(reinterpret_cast<const uint32_t *>(smem + L.off_planes),
-                            reinterpret_cast<uint16_t *>(O), reinterpret_cast<uint8_t *>(O), E == 2, list, F, TW,
-                            BH, L.pw, NB, XOFF);
+        plain_strip_store<T>(cf, O, x0, y0, TW, r0, SR, lane);
       }
-    }
-
-    if (tma_out) {
-      fence_proxy_async_smem();
-      __syncthreads();
-      if (tid == 0) tma_store_2d(&cf->tout, O, x0, y0);
-    } else {
-      __syncthreads();
-      plain_tile_store<T>(cf, O, x0, y0, TW, TH);
-    }
-    if (tid == 0) {
-      bulk_commit();
-      if (misc[0] != 0) {
-        unsigned long long *ctr = cf->flagged;
-        if (ctr != nullptr) atomicAdd(ctr, static_cast<unsigned long long>(misc[0]));
+      if (lane == 0) {
+        bulk_commit();
+        if (flagged != 0 && cur.counted) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       }
+    } else if (ALGO != ALGO_DENSE3 && lane == 0) {
+      bulk_commit();  // keep one bulk group per tile so the wait above stays exact
     }
-    fence_proxy_async_smem();  // generic writes to this stage precede the TMA that will refill it
-    __syncthreads();
+    fence_proxy_async_smem();  // this warp's generic writes to the stage precede its refill by TMA
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
-  if (tid == 0) bulk_wait_all<0>();
+  if (lane == 0) bulk_wait_all<0>();
 }
 
 template <typename T, int K>

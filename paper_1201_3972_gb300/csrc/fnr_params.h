@@ -7,7 +7,8 @@
 
 namespace fnr {
 
-constexpr int kThreads = 256;          // threads per CTA for every kernel
+constexpr int kConsumerWarps = 8;      // warps that filter; each owns a strip of tile_h / 8 rows
+constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + one producer warp (tile loads)
 constexpr int kMaxK = 21;              // largest window built
 constexpr int kNumK = (kMaxK - 3) / 2 + 1;
 constexpr int kDirMax = 512;           // frames whose tile ranges a CTA keeps in shared memory
@@ -22,7 +23,7 @@ constexpr int kFrameTmaOut = 2;    // store tiles with TMA
 // 128-byte alignment.
 struct alignas(128) FrameDev {
   CUtensorMap tin;                 // box = (tile_w + 2*xoff) x (tile_h + 2r), u8/u16
-  CUtensorMap tout;                // box = tile_w x tile_h
+  CUtensorMap tout;                // box = tile_w x (tile_h / kConsumerWarps): one warp's strip
   const unsigned char *in;
   unsigned char *out;
   long long in_pitch;
@@ -54,16 +55,27 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
   return align_up(r, 16 / esize);
 }
 
+// Rows per vertical/horizontal extreme group of the compacted strategies.
+__host__ __device__ constexpr int row_group(int k) { return k >= 8 ? 8 : (k >= 4 ? 4 : 2); }
+
+// tile_h must split into kConsumerWarps strips, each a whole number of row
+// groups (compacted strategies) or of row pairs (dense 3x3).
+__host__ __device__ constexpr int tile_h_multiple(int k, int algo) {
+  return kConsumerWarps * (algo == ALGO_DENSE3 ? 2 : row_group(k));
+}
+
 // Shared-memory layout of one CTA (byte offsets). Identical on host and device.
+// Per CTA: two staging buffers and two output tiles; per consumer warp: its
+// flagged list, vertical extremes and (bit-plane strategy) bit planes.
 struct Layout {
-  int r, bw, bh, vw, pw, nbmax;
+  int r, bw, bh, vw, pw, nbmax, sr;
   int off_stage[2];
   int off_out[2];
-  int off_list;
-  int off_vmin, off_vmax;
-  int off_planes;
-  int off_bar;
-  int off_misc;
+  int off_warp;        // first per-warp block
+  int warp_bytes;      // size of one per-warp block
+  int w_list, w_vmin, w_vmax, w_planes;  // offsets inside a per-warp block
+  int plane_rows;      // rows of bit planes a warp builds (its strip + halo)
+  int off_bar;         // full[2], empty[2]
   int off_info;
   int off_dir;
   int total;
@@ -78,24 +90,29 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   L.vw = tile_w + 2 * L.r;
   L.pw = (L.bw + 31) / 32 + 1;
   L.nbmax = 8 * esize;
+  L.sr = tile_h / kConsumerWarps;
+  L.plane_rows = L.sr + k - 1;
   int off = 0;
   const int stage = align_up(L.bw * L.bh * esize, 128);
-  const int outb = align_up(tile_w * tile_h * esize, 128);
+  // the dense 3x3 strategy writes results straight from registers: no output tile
+  const int outb = algo == ALGO_DENSE3 ? 0 : align_up(tile_w * tile_h * esize, 128);
   L.off_stage[0] = off; off += stage;
   L.off_stage[1] = off; off += stage;
   L.off_out[0] = off; off += outb;
   L.off_out[1] = off; off += outb;
-  L.off_list = L.off_vmin = L.off_vmax = L.off_planes = -1;
+  L.w_list = L.w_vmin = L.w_vmax = L.w_planes = -1;
+  int w = 0;
   if (algo != ALGO_DENSE3) {
-    L.off_list = off; off += align_up(tile_w * tile_h * 2, 128);
-    L.off_vmin = off; off += align_up(tile_h * L.vw * 2, 128);
-    L.off_vmax = off; off += align_up(tile_h * L.vw * 2, 128);
+    L.w_list = w; w += align_up(L.sr * tile_w * 2, 16);
+    L.w_vmin = w; w += align_up(L.sr * L.vw * 2, 16);
+    L.w_vmax = w; w += align_up(L.sr * L.vw * 2, 16);
   }
   if (algo == ALGO_BITPLANE) {
-    L.off_planes = off; off += align_up(L.nbmax * L.bh * L.pw * 4, 128);
+    L.w_planes = w; w += align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);
   }
-  L.off_bar = off; off += 16;
-  L.off_misc = off; off += 16;
+  L.warp_bytes = align_up(w, 128);
+  L.off_warp = off; off += kConsumerWarps * L.warp_bytes;
+  L.off_bar = off; off += 32;
   L.off_info = off; off += 64;
   L.off_dir = off; off += kDirMax * 4;
   L.total = align_up(off, 128);

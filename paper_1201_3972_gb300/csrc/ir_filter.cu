@@ -146,7 +146,7 @@ static ir_kernel_config default_config(int esize, int k) {
   } else {
     c.algo = IR_ALGO_BITPLANE;
     c.tile_w = 64;
-    c.tile_h = 32;
+    c.tile_h = 64;
   }
   (void)esize;
   return c;
@@ -165,6 +165,8 @@ static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_conf
   if (c.algo == IR_ALGO_NETWORK && k > 7) return no("NETWORK is built for k <= 7");
   if (c.algo != IR_ALGO_DENSE3 && c.algo != IR_ALGO_NETWORK && c.algo != IR_ALGO_BITPLANE) return no("unknown algo");
   if (c.ctas_per_sm < 0) return no("ctas_per_sm < 0");
+  if (c.tile_h % tile_h_multiple(k, c.algo)) return no("tile_h must split into 8 warp strips of whole row groups");
+  if (c.algo == IR_ALGO_DENSE3 && ((c.tile_w / 8) & (c.tile_w / 8 - 1))) return no("DENSE3 needs tile_w / 8 a power of two");
   const Layout L = make_layout(esize, k, c.algo, c.tile_h, c.tile_w);
   if (L.bw > 256 || L.bh > 256) return no("tile plus halo exceeds the 256-pixel TMA box");
   if (c.tile_w > 256 || c.tile_h > 256) return no("tile side > 256");
@@ -231,7 +233,7 @@ void fnr::host_make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t 
   if (box_ok && tma_addressable(in, in_pitch) && encode_map(h, &f.tin, esize, in, H, W, in_pitch, L.bw, L.bh))
     f.flags |= kFrameTmaIn;
   if (box_ok && tma_addressable(out, out_pitch) &&
-      encode_map(h, &f.tout, esize, out, H, W, out_pitch, c.tile_w, c.tile_h))
+      encode_map(h, &f.tout, esize, out, H, W, out_pitch, c.tile_w, c.tile_h / kConsumerWarps))
     f.flags |= kFrameTmaOut;
 }
 
@@ -610,18 +612,17 @@ static std::vector<ir_kernel_config> candidates(int esize, int k) {
   std::vector<ir_kernel_config> out;
   auto add = [&](int algo, int tw, int th) { out.push_back(ir_kernel_config{tw, th, algo, 0}); };
   if (k == 3) {
-    for (int tw : {64, 128, 192})
-      for (int th : {16, 32, 64}) add(IR_ALGO_DENSE3, tw, th);
-    add(IR_ALGO_NETWORK, 64, 32);
-    add(IR_ALGO_BITPLANE, 64, 32);
+    for (int tw : {32, 64, 128})
+      for (int th : {32, 64, 128}) add(IR_ALGO_DENSE3, tw, th);
+    add(IR_ALGO_NETWORK, 64, 64);
+    add(IR_ALGO_BITPLANE, 64, 64);
   } else if (k <= 7) {
     for (int tw : {32, 64, 128})
-      for (int th : {16, 32}) add(IR_ALGO_NETWORK, tw, th);
-    add(IR_ALGO_BITPLANE, 64, 32);
-    add(IR_ALGO_BITPLANE, 128, 32);
+      for (int th : {32, 64, 128}) add(IR_ALGO_NETWORK, tw, th);
+    add(IR_ALGO_BITPLANE, 64, 64);
   } else {
     for (int tw : {32, 64, 128})
-      for (int th : {16, 32, 64}) add(IR_ALGO_BITPLANE, tw, th);
+      for (int th : {64, 128}) add(IR_ALGO_BITPLANE, tw, th);
   }
   (void)esize;
   return out;

@@ -91,7 +91,7 @@ const void *kernel_for_k(int esize, int k, int algo) {
 void static_config(int k, int &algo, int &tw, int &th) {
   algo = k == 3 ? ALGO_DENSE3 : (k <= 7 ? ALGO_NETWORK : ALGO_BITPLANE);
   tw = k == 3 ? 128 : 64;
-  th = k <= 7 ? 64 : 32;
+  th = 64;
 }
 
 // One-time set-up of `dev` (the current device). Called under g_mu.
@@ -187,7 +187,7 @@ extern "C" ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pit
   f.flags = 0;
   if (encode(&f.tin, esize, st.scratch, H, W, spitch, L.bw, L.bh)) f.flags |= kFrameTmaIn;
   const bool out_ok = (reinterpret_cast<uintptr_t>(frame) % 16) == 0 && pitch_bytes % 16 == 0;
-  if (out_ok && encode(&f.tout, esize, frame, H, W, pitch_bytes, tw, th)) f.flags |= kFrameTmaOut;
+  if (out_ok && encode(&f.tout, esize, frame, H, W, pitch_bytes, tw, th / kConsumerWarps)) f.flags |= kFrameTmaOut;
   prm.table = nullptr;
   prm.nframes = 1;
   prm.total_tiles = f.tiles_x * f.tiles_y;
