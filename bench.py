@@ -275,6 +275,8 @@ def own_arm(args):
         "gpu_launches": int(gpu_launches), "launches_per_step": launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
+    if rank == 0 and args.batch_leg:
+        result["batch_mixed"] = batch_leg(flt, stream, args)
     if rank == 0 and args.serve_seconds > 0:
         result["serve"] = serve_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline:
@@ -286,6 +288,37 @@ def own_arm(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batch_leg(flt, stream, args):
+    """The mixed batch: 256 frames, sizes 160x120..1920x1080, u8 and 14-bit,
+    windows 3/5/7/9/15, 5-30% salt-and-pepper, one graph launch per step;
+    also its k=3/5 subset (the HBM-bound classes)."""
+    import torch
+    from paper_1201_3972_gb300 import _lib, synth
+    specs = synth.workload_batch()
+    frames = [s.make() for s in specs]
+    bufs = []
+    for f in frames:
+        src = torch.from_numpy(f.view(np.int16) if f.dtype == np.uint16 else f).cuda()
+        bufs.append((src, torch.empty_like(src)))
+    out = {}
+    for name, sel in (("all", lambda s: True), ("k3_k5", lambda s: s.k in (3, 5))):
+        idx = [i for i, s in enumerate(specs) if sel(s)]
+        plan = flt.plan([{"in": bufs[i][0], "out": bufs[i][1], "k": specs[i].k, "u14": specs[i].dtype == synth.U14}
+                         for i in idx])
+        for _ in range(args.warmup):
+            plan.launch(stream)
+        durs = time_events(torch, lambda: plan.launch(stream), max(5, args.steps), stream)
+        ms = statistics.median(durs)
+        px = sum(specs[i].pixels for i in idx)
+        byts = sum(2 * specs[i].pixels * specs[i].esize for i in idx)
+        hbm, _ = peaks()
+        out[name] = {"frames": len(idx), "mpx": round(px / 1e6, 1), "ms": round(ms, 4),
+                     "mpx_s": round(px / ms / 1e3, 1), "hbm_frac": round(byts / (ms * 1e-3) / 1e9 / hbm, 4),
+                     "kernels_per_launch": plan.kernel_count}
+        plan.close()
+    return out
 
 
 def serve_leg(args, device):
@@ -384,6 +417,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
+    ap.add_argument("--batch-leg", action="store_true", help="also time the 256-frame mixed batch")
     ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -58,7 +58,7 @@ typedef enum { IR_U8 = 0, IR_U16 = 1, IR_U14 = 2 } ir_dtype;
 typedef enum {
   IR_ALGO_AUTO = 0,          /* tuned choice for (dtype, k) */
   IR_ALGO_DENSE3 = 1,        /* k = 3 only: median for every pixel with shared column sorts, packed 16x2 */
-  IR_ALGO_NETWORK = 2,       /* k <= 7: flagged pixels compacted, register selection network each */
+  IR_ALGO_NETWORK = 2,       /* k <= 9: flagged pixels compacted, register selection network each */
   IR_ALGO_BITPLANE = 3       /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
 } ir_algo;
 

@@ -569,15 +569,13 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
         seg[a] = __funnelshift_r(P[a * PW], P[a * PW + 1], sh);
         cnt += __popc(alive[a] & ~seg[a]);
       }
-      if (rank < cnt) {
+      // keep the 0-bit pixels when the rank falls among them, else the 1-bit ones
+      const bool one = rank >= cnt;
+      const uint32_t flip = one ? 0u : 0xffffffffu;
+      rank -= one ? cnt : 0u;
+      res |= (one ? 1u : 0u) << b;
 #pragma unroll
-        for (int a = 0; a < K; ++a) alive[a] &= ~seg[a];
-      } else {
-        rank -= cnt;
-        res |= 1u << b;
-#pragma unroll
-        for (int a = 0; a < K; ++a) alive[a] &= seg[a];
-      }
+      for (int a = 0; a < K; ++a) alive[a] &= seg[a] ^ flip;
     }
     O[(r0 + q) * TW + tx] = static_cast<T>(res);
   }
@@ -586,13 +584,14 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
-template <int ALGO>
+template <int ALGO, int K>
 struct MinBlocks {
-  static constexpr int value = ALGO == ALGO_BITPLANE ? 1 : 3;
+  // the 81-input network of k = 9 needs about 96 registers
+  static constexpr int value = (ALGO == ALGO_BITPLANE || K >= 9) ? 2 : 3;
 };
 
 template <typename T, int K, int ALGO>
-__global__ void __launch_bounds__(kThreads, MinBlocks<ALGO>::value) fnr_kernel(const __grid_constant__ FnrParams p) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kernel(const __grid_constant__ FnrParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int E = sizeof(T);
   constexpr int R = (K - 1) / 2;
@@ -751,7 +750,7 @@ inline const void *kernel_for(int algo) {
       if constexpr (K == 3) return reinterpret_cast<const void *>(&fnr_kernel<T, 3, ALGO_DENSE3>);
       return nullptr;
     case ALGO_NETWORK:
-      if constexpr (K <= 7) return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_NETWORK>);
+      if constexpr (K <= 9) return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_NETWORK>);
       return nullptr;
     case ALGO_BITPLANE:
       return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_BITPLANE>);

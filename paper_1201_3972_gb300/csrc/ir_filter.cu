@@ -139,7 +139,7 @@ static ir_kernel_config default_config(int esize, int k) {
     c.algo = IR_ALGO_DENSE3;
     c.tile_w = 128;
     c.tile_h = 64;
-  } else if (k <= 7) {
+  } else if (k <= 9) {
     c.algo = IR_ALGO_NETWORK;
     c.tile_w = 64;
     c.tile_h = 64;
@@ -162,7 +162,7 @@ static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_conf
   // halo) and every box row must be a whole number of 16-byte units
   if ((c.tile_w * esize) % 16) return no("tile_w * bytes per pixel must be a multiple of 16");
   if (c.algo == IR_ALGO_DENSE3 && k != 3) return no("DENSE3 is the 3x3 window only");
-  if (c.algo == IR_ALGO_NETWORK && k > 7) return no("NETWORK is built for k <= 7");
+  if (c.algo == IR_ALGO_NETWORK && k > 9) return no("NETWORK is built for k <= 9");
   if (c.algo != IR_ALGO_DENSE3 && c.algo != IR_ALGO_NETWORK && c.algo != IR_ALGO_BITPLANE) return no("unknown algo");
   if (c.ctas_per_sm < 0) return no("ctas_per_sm < 0");
   if (c.tile_h % tile_h_multiple(k, c.algo)) return no("tile_h must split into 8 warp strips of whole row groups");
@@ -623,6 +623,9 @@ static std::vector<ir_kernel_config> candidates(int esize, int k) {
   } else {
     for (int tw : {32, 64, 128})
       for (int th : {64, 128}) add(IR_ALGO_BITPLANE, tw, th);
+    if (k <= 9)
+      for (int tw : {32, 64})
+        for (int th : {64, 128}) add(IR_ALGO_NETWORK, tw, th);
   }
   (void)esize;
   return out;

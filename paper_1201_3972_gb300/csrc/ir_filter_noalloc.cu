@@ -89,7 +89,7 @@ const void *kernel_for_k(int esize, int k, int algo) {
 }
 
 void static_config(int k, int &algo, int &tw, int &th) {
-  algo = k == 3 ? ALGO_DENSE3 : (k <= 7 ? ALGO_NETWORK : ALGO_BITPLANE);
+  algo = k == 3 ? ALGO_DENSE3 : (k <= 9 ? ALGO_NETWORK : ALGO_BITPLANE);
   tw = k == 3 ? 128 : 64;
   th = 64;
 }

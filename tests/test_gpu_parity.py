@@ -32,7 +32,7 @@ def flt():
 
 def algos_for(k):
     out = [_lib.IR_ALGO_BITPLANE]
-    if k <= 7:
+    if k <= 9:
         out.append(_lib.IR_ALGO_NETWORK)
     if k == 3:
         out.append(_lib.IR_ALGO_DENSE3)
