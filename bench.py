@@ -277,6 +277,9 @@ def own_arm(args):
     }
     if rank == 0 and args.batch_leg:
         result["batch_mixed"] = batch_leg(flt, stream, args)
+    if rank == 0 and not args.no_quality:
+        from paper_1201_3972_gb300 import quality
+        result["table1_synthetic"] = quality.table1(flt)
     if rank == 0 and args.serve_seconds > 0:
         result["serve"] = serve_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline:
@@ -418,6 +421,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
     ap.add_argument("--batch-leg", action="store_true", help="also time the 256-frame mixed batch")
+    ap.add_argument("--no-quality", action="store_true", help="skip the Table 1 style PSNR comparison")
     ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -98,6 +98,23 @@ ir_status ir_filter_run2(ir_filter *h, const void *in, size_t in_pitch, void *ou
                          int H, int W, ir_dtype dtype, int k, void *cuda_stream,
                          unsigned long long *flagged_count);
 
+/* The standard median filter the paper compares FNR against (Sec. 2, Table 1:
+ * "MF"): every pixel is replaced by the median of its k x k window (replicate
+ * border), no detection step. Arguments as ir_filter_run2; `median_count`
+ * (nullable device pointer) is set to H * W, the number of medians taken. */
+ir_status ir_filter_median_filter(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch,
+                                  int H, int W, ir_dtype dtype, int k, void *cuda_stream,
+                                  unsigned long long *median_count);
+
+/* Iterative FNR (Figs. 3-6 apply FNR twice): `passes` non-recursive passes,
+ * each reading the previous pass's output, the last one written to `out`.
+ * passes in [1, 64]; more than one pass uses handle scratch of H rows of
+ * W * bytes per pixel. `flagged_per_pass` (nullable) is a DEVICE array of
+ * `passes` counters, entry p set to the number of noisy pixels of pass p. */
+ir_status ir_filter_run_passes(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch,
+                               int H, int W, ir_dtype dtype, int k, int passes, void *cuda_stream,
+                               unsigned long long *flagged_per_pass);
+
 /* One frame of a batch: same meaning as the arguments of ir_filter_run2. */
 typedef struct {
   const void *in;

@@ -49,6 +49,8 @@ def _load():
         lib.oracle_fnr_mt.restype = ll
         lib.oracle_fnr_stack.argtypes = [vp, vp, ll, i32, i32, i32, i32, i32]
         lib.oracle_fnr_stack.restype = ll
+        lib.oracle_median_filter.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32]
+        lib.oracle_median_filter.restype = ll
         lib.oracle_introsort.argtypes = [vp, ctypes.c_long, i32]
         lib.oracle_introsort.restype = None
         _lib = lib
@@ -105,6 +107,31 @@ def fnr_stack(frames: np.ndarray, k: int):
     if f < 0:
         raise ValueError("oracle rejected arguments")
     return out, int(f)
+
+
+def median_filter(frame: np.ndarray, k: int):
+    """The standard median filter (Sec. 2, Table 1 "MF"): every pixel takes its
+    window median. Returns (filtered frame, number of medians)."""
+    lib = _load()
+    es = _check_frame(frame)
+    out = np.empty(frame.shape, dtype=frame.dtype)
+    H, W = frame.shape
+    f = lib.oracle_median_filter(frame.ctypes.data, frame.strides[0], out.ctypes.data, out.strides[0],
+                                 H, W, es, int(k))
+    if f < 0:
+        raise ValueError("oracle rejected arguments")
+    return out, int(f)
+
+
+def fnr_passes(frame: np.ndarray, k: int, passes: int, threads: int = 1):
+    """Iterative FNR (Figs. 3-6 use two passes): each pass filters the previous
+    pass's output. Returns (final frame, flagged count of every pass)."""
+    counts = []
+    cur = frame
+    for _ in range(int(passes)):
+        cur, f = fnr_mt(cur, k, threads) if threads > 1 else fnr(cur, k)
+        counts.append(f)
+    return cur, counts
 
 
 def introsort(values, depth_limit: int = -1) -> np.ndarray:

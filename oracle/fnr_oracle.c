@@ -224,6 +224,34 @@ long long oracle_fnr_stack(const void *in, void *out, long long pitch, int count
     return total;
 }
 
+/* The standard median filter the paper compares FNR with (Sec. 2, Table 1,
+ * "MF"): every pixel, noisy or not, is replaced by the median of S_xy,
+ * found the same way (introsort, element (n-1)/2). Returns the number of
+ * medians taken (H*W), or -1 for bad arguments. */
+long long oracle_median_filter(const void *in, long long in_pitch, void *out, long long out_pitch,
+                               int H, int W, int esize, int k)
+{
+    if (!args_ok(in, in_pitch, out, out_pitch, H, W, esize, k)) return -1;
+    const int r = (k - 1) / 2;
+    const int n = k * k;
+    uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!w) return -1;
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int i = 0;
+            for (int dy = -r; dy <= r; dy++) {
+                int yy = clampi(y + dy, 0, H - 1);
+                for (int dx = -r; dx <= r; dx++)
+                    w[i++] = load_px((const unsigned char *)in, in_pitch, esize, yy, clampi(x + dx, 0, W - 1));
+            }
+            oracle_introsort(w, n, -1);
+            store_px((unsigned char *)out, out_pitch, esize, y, x, w[(n - 1) / 2]);
+        }
+    }
+    free(w);
+    return (long long)H * W;
+}
+
 /* Same result, rows split into contiguous bands over `threads` POSIX threads
  * (used only to time the oracle on all host cores). */
 typedef struct {

@@ -27,7 +27,7 @@ EXPORTED = (
     "ir_batch_plan_create", "ir_batch_plan_launch", "ir_batch_plan_kernel_count", "ir_batch_plan_destroy",
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
-    "ir_filter_run_noalloc",
+    "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
     "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
@@ -112,6 +112,8 @@ def load(path: Optional[str] = None):
             "ir_filter_last_error": ([vp], ctypes.c_char_p),
             "ir_filter_version": ([], ctypes.c_char_p),
             "ir_filter_run_noalloc": ([vp, i32, i32, sz, i32, i32, vp], i32),
+            "ir_filter_median_filter": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
+            "ir_filter_run_passes": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, i32, vp, vp], i32),
             "ir_server_create": ([i32, ctypes.POINTER(ir_server_config), ctypes.POINTER(vp)], i32),
             "ir_server_destroy": ([vp], None),
             "ir_server_filter": ([vp], vp),
@@ -216,6 +218,30 @@ class Filter:
                        stream=None, flagged_count=None) -> None:
         _check(self.lib, self.h, self.lib.ir_filter_run2(self.h, _ptr(src), in_pitch, _ptr(dst), out_pitch, H, W,
                                                          dtype, k, _stream(stream), _ptr(flagged_count) or None))
+
+    def ir_filter_median_filter(self, src, in_pitch: int, dst, out_pitch: int, H: int, W: int, dtype: int, k: int,
+                                stream=None, median_count=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_median_filter(self.h, _ptr(src), in_pitch, _ptr(dst), out_pitch,
+                                                                  H, W, dtype, k, _stream(stream),
+                                                                  _ptr(median_count) or None))
+
+    def ir_filter_run_passes(self, src, in_pitch: int, dst, out_pitch: int, H: int, W: int, dtype: int, k: int,
+                             passes: int, stream=None, flagged_per_pass=None) -> None:
+        _check(self.lib, self.h, self.lib.ir_filter_run_passes(self.h, _ptr(src), in_pitch, _ptr(dst), out_pitch, H,
+                                                               W, dtype, k, passes, _stream(stream),
+                                                               _ptr(flagged_per_pass) or None))
+
+    def median_filter(self, src, dst, k: int, u14: bool = False, stream=None, median_count=None) -> None:
+        """Standard median filter (every pixel), the paper's MF baseline."""
+        H, W, ip = _frame_geometry(src)
+        _, _, op = _frame_geometry(dst)
+        self.ir_filter_median_filter(src, ip, dst, op, H, W, dtype_code(src, u14), k, stream, median_count)
+
+    def run_passes(self, src, dst, k: int, passes: int, u14: bool = False, stream=None, flagged_per_pass=None):
+        """Iterative FNR: `passes` passes, the last written to dst."""
+        H, W, ip = _frame_geometry(src)
+        _, _, op = _frame_geometry(dst)
+        self.ir_filter_run_passes(src, ip, dst, op, H, W, dtype_code(src, u14), k, passes, stream, flagged_per_pass)
 
     def run(self, frame, k: int, u14: bool = False, stream=None) -> None:
         """In-place filter of a 2-D uint8/uint16 CUDA tensor."""

@@ -306,7 +306,7 @@ __device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint3
 // frame is 16-byte aligned, else per-pixel stores clipped to the frame.
 // tw_valid, th_valid: the part of the tile inside the frame. tile_w / 8 is a
 // power of two (seg_shift = log2 of it).
-template <typename T, bool COUNT>
+template <typename T, bool COUNT, bool ALL>
 __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int TW, int BW, int r0, int SR,
                              int seg_shift, int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged) {
   constexpr int XOFF = xoff_for(1, sizeof(T));
@@ -352,7 +352,7 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
         const uint32_t gmax = vmax2(vmax2(ohi[pp], mhi), ohi[pp + 1]);
         const uint32_t gm = med3v(maxlo, medmd, minhi);
         const uint32_t c = e[1 + o][pp + 1];
-        const uint32_t sig = signal_bits(c, gmin, gmax);
+        const uint32_t sig = ALL ? 0u : signal_bits(c, gmin, gmax);  // ALL: standard median filter
         const uint32_t keep = sig * 0xffffu;
         res[pp] = (c & keep) | (gm & ~keep);
         if constexpr (COUNT) {
@@ -436,7 +436,8 @@ __device__ void vertical_strip(const T *S, uint16_t *vmin, uint16_t *vmax, int B
 // (row in strip << 8 | column). Returns the list length (warp-uniform).
 template <typename T, int K>
 __device__ int horizontal_flag_strip(const T *S, const uint16_t *vmin, const uint16_t *vmax, T *O, uint16_t *list,
-                                     int TW, int BW, int VW, int r0, int SR, int tw_valid, int th_valid, int lane) {
+                                     int TW, int BW, int VW, int r0, int SR, int tw_valid, int th_valid, bool all,
+                                     int lane) {
   constexpr int R = (K - 1) / 2, RG = row_group(K);
   constexpr int XOFF = xoff_for(R, sizeof(T));
   const int per_row = TW / RG;
@@ -465,7 +466,7 @@ __device__ int horizontal_flag_strip(const T *S, const uint16_t *vmin, const uin
         const uint32_t c = crow[q];
         O[ty * TW + tx0 + q] = static_cast<T>(c);
         const bool inside = ty < th_valid && tx0 + q < tw_valid;
-        fm |= static_cast<uint32_t>(inside && (c == gmin[q] || c == gmax[q])) << q;
+        fm |= static_cast<uint32_t>(inside && (all || c == gmin[q] || c == gmax[q])) << q;
       }
     }
     const int cnt = __popc(fm);
@@ -689,14 +690,21 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       // results go straight from registers to the frame (no output tile)
       const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
-      if (cur.counted) {
-        dense3_strip<T, true>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                              flagged);
+      if (p.mode == kModeMedian) {
+        dense3_strip<T, false, true>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
+                                     flagged);
+        if (cur.counted && lane == 0) {  // every in-frame pixel of the strip takes a median
+          const int rows = min(SR, cur.H - y0 - r0), cols = min(TW, cur.W - x0);
+          atomicAdd(cf->flagged, static_cast<unsigned long long>(rows) * static_cast<unsigned long long>(cols));
+        }
+      } else if (cur.counted) {
+        dense3_strip<T, true, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
+                                     flagged);
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if (lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else {
-        dense3_strip<T, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                               flagged);
+        dense3_strip<T, false, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
+                                      lane, flagged);
       }
     } else if (live) {
       if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         vertical_strip<T, K>(S, vmin, vmax, BW, L.vw, r0, SR, lane);
         __syncwarp();
         flagged = horizontal_flag_strip<T, K>(S, vmin, vmax, O, list, TW, BW, L.vw, r0, SR, cur.W - x0, cur.H - y0,
-                                              lane);
+                                              p.mode == kModeMedian, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {

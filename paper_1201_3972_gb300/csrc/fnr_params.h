@@ -43,7 +43,11 @@ struct alignas(128) FnrParams {
   int tile_w, tile_h;
   unsigned int *status;            // device status word (bit 0: bounded wait timed out)
   unsigned long long *launches;    // device launch counter (nullable)
+  int mode;                        // kModeFnr, or kModeMedian: every pixel is treated as noisy
 };
+
+constexpr int kModeFnr = 0;        // replace only pixels equal to a window extreme (Sec. 3.3-3.4)
+constexpr int kModeMedian = 1;     // standard median filter: replace every pixel (the paper's MF, Sec. 2)
 
 constexpr unsigned int kStatusTimeout = 1u;
 

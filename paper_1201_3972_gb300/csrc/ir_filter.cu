@@ -295,7 +295,7 @@ static ir_status ensure_scratch(ir_filter *h, size_t bytes) {
 }
 
 static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H, int W,
-                         ir_dtype dtype, int k, cudaStream_t st, unsigned long long *flagged) {
+                         ir_dtype dtype, int k, cudaStream_t st, unsigned long long *flagged, int mode = kModeFnr) {
   ClassLaunch cl;
   cl.esize = esize_of(dtype);
   cl.k = k;
@@ -309,6 +309,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.prm.tile_h = cl.cfg.tile_h;
   cl.prm.status = h->d_status;
   cl.prm.launches = h->d_launches;
+  cl.prm.mode = mode;
   ir_status s = host_prepare_class(h, cl);
   if (s != IR_OK) return s;
   if (flagged) IR_CUDA(h, cudaMemsetAsync(flagged, 0, sizeof(unsigned long long), st));
@@ -408,6 +409,46 @@ ir_status ir_filter_run(ir_filter *h, void *frame, int H, int W, size_t pitch_by
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   IR_CUDA(h, cudaMemcpy2DAsync(h->scratch, spitch, frame, pitch_bytes, row, H, cudaMemcpyDeviceToDevice, st));
   return run_one(h, h->scratch, spitch, frame, pitch_bytes, H, W, dtype, k, st, nullptr);
+}
+
+ir_status ir_filter_median_filter(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H,
+                                  int W, ir_dtype dtype, int k, void *cuda_stream, unsigned long long *median_count) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
+  if (s != IR_OK) return s;
+  DeviceGuard g(h->device);
+  return run_one(h, in, in_pitch, out, out_pitch, H, W, dtype, k, static_cast<cudaStream_t>(cuda_stream),
+                 median_count, kModeMedian);
+}
+
+ir_status ir_filter_run_passes(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H,
+                               int W, ir_dtype dtype, int k, int passes, void *cuda_stream,
+                               unsigned long long *flagged_per_pass) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (passes < 1 || passes > 64) return fail(h, IR_EINVAL, "passes must be in [1, 64] (got %d)", passes);
+  ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
+  if (s != IR_OK) return s;
+  DeviceGuard g(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (passes == 1) return run_one(h, in, in_pitch, out, out_pitch, H, W, dtype, k, st, flagged_per_pass);
+  // ping-pong between `out` and handle scratch, arranged so the last pass writes `out`
+  const size_t row = static_cast<size_t>(W) * esize_of(dtype);
+  const size_t spitch = (row + 255) / 256 * 256;
+  s = ensure_scratch(h, spitch * static_cast<size_t>(H));
+  if (s != IR_OK) return s;
+  const void *src = in;
+  size_t src_pitch = in_pitch;
+  for (int p = 0; p < passes; ++p) {
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    void *dst = to_out ? out : h->scratch;
+    const size_t dst_pitch = to_out ? out_pitch : spitch;
+    s = run_one(h, src, src_pitch, dst, dst_pitch, H, W, dtype, k, st,
+                flagged_per_pass ? flagged_per_pass + p : nullptr);
+    if (s != IR_OK) return s;
+    src = dst;
+    src_pitch = dst_pitch;
+  }
+  return IR_OK;
 }
 
 ir_status ir_filter_sync_status(ir_filter *h) {

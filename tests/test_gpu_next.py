@@ -1,0 +1,87 @@
+"""GPU parity of the next rows: the standard median filter (the paper's MF
+baseline) and iterative FNR, against the CPU oracle bit for bit, plus the
+paper's qualitative Table 1 claim on synthetic frames."""
+import numpy as np
+import pytest
+
+import oracle
+from _dev import download, empty_like_frame, upload
+from paper_1201_3972_gb300 import _lib, quality, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def flt():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1201_3972_gb300 import _build
+    _build.build()
+    f = _lib.Filter(0)
+    yield f
+    f.sync_status()
+    f.close()
+
+
+def _algos(k):
+    out = [_lib.IR_ALGO_BITPLANE]
+    if k <= 9:
+        out.append(_lib.IR_ALGO_NETWORK)
+    if k == 3:
+        out.append(_lib.IR_ALGO_DENSE3)
+    return out
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 9, 15, 21])
+def test_median_filter_matches_oracle(flt, k):
+    import torch
+    rng = np.random.default_rng(40 + k)
+    frames = [rng.integers(0, 256, (45, 133)).astype(np.uint8),
+              synth.make_frame(70, 96, synth.U14, 9, 8.0, 0.2)]
+    for f in frames:
+        dt = _lib.IR_U8 if f.dtype == np.uint8 else _lib.IR_U16
+        want, n = oracle.median_filter(f, k)
+        for algo in _algos(k):
+            flt.set_config(dt, k, 64, 64, algo)
+            ib, ia, ip = upload(f)
+            ob, oa, op = empty_like_frame(f)
+            ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+            flt.ir_filter_median_filter(ia, ip, oa, op, f.shape[0], f.shape[1], dt, k, None, ctr)
+            np.testing.assert_array_equal(download(ob, oa, op, f.shape[0], f.shape[1], f.dtype), want)
+            assert int(ctr.item()) == n == f.size
+        flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+@pytest.mark.parametrize("passes", [1, 2, 3, 4])
+def test_iterative_passes_match_oracle(flt, passes):
+    import torch
+    for s in (synth.workload_single_u8()[0], synth.workload_sweep_u14()[7]):
+        f = s.make()
+        want, counts = oracle.fnr_passes(f, s.k, passes, threads=16)
+        ib, ia, ip = upload(f)
+        ob, oa, op = empty_like_frame(f)
+        ctr = torch.zeros(passes, dtype=torch.int64, device="cuda")
+        flt.ir_filter_run_passes(ia, ip, oa, op, f.shape[0], f.shape[1], s.dtype, s.k, passes, None, ctr)
+        np.testing.assert_array_equal(download(ob, oa, op, f.shape[0], f.shape[1], f.dtype), want)
+        assert [int(v) for v in ctr.cpu().tolist()] == counts
+
+
+def test_passes_rejects_bad_count(flt):
+    import torch
+    a = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(_lib.IrError):
+        flt.ir_filter_run_passes(int(a.data_ptr()), 8, int(a.data_ptr()) + 32, 8, 2, 8, _lib.IR_U8, 3, 0)
+
+
+def test_table1_ordering_on_synthetic_frames(flt):
+    """Table 1's qualitative result: FNR gives a higher PSNR than MF at 20% and
+    30% impulses, takes medians only for the flagged pixels (fewer sorts than
+    MF's one per pixel), and a second pass helps both."""
+    res = quality.table1(flt)
+    H, W = 244, 364
+    for key, r in res.items():
+        assert r["fnr1_psnr"] > r["mf1_psnr"] > r["noisy_psnr"], (key, r)
+        assert r["fnr2_psnr"] > r["mf2_psnr"], (key, r)
+        assert r["fnr2_psnr"] > r["fnr1_psnr"], (key, r)
+        assert r["mf1_sorts"] == [H * W]
+        assert r["fnr1_sorts"][0] < H * W

@@ -128,6 +128,38 @@ def test_matches_library_filters_on_synthetic_frames(oracle_mod):
             assert gf == wf
 
 
+@pytest.mark.parametrize("dtype", [synth.U8, synth.U16])
+def test_median_filter_matches_library(oracle_mod, dtype):
+    """The MF baseline (every pixel takes its window median) equals scipy's
+    median filter with a replicated border."""
+    rng = np.random.default_rng(11 + dtype)
+    for H, W in ((1, 1), (3, 9), (13, 17), (20, 23)):
+        for k in (3, 5, 7, 9, 15, 21):
+            for style in ("uniform", "few"):
+                a = rand_frame(rng, H, W, dtype, style)
+                got, n = oracle_mod.median_filter(a, k)
+                np.testing.assert_array_equal(got, nd.median_filter(a, size=k, mode="nearest"))
+                assert n == a.size
+
+
+def test_iterative_passes_are_compositions(oracle_mod):
+    """Two and three passes equal the library-filter definition applied
+    repeatedly, with the flagged count of each pass."""
+    rng = np.random.default_rng(12)
+    a = rand_frame(rng, 30, 41, synth.U8, "smooth_sp")
+    for k in (3, 5):
+        cur, want_counts = a, []
+        for _ in range(3):
+            cur, c = library_fnr(cur, k)
+            want_counts.append(c)
+        got, counts = oracle_mod.fnr_passes(a, k, 3)
+        np.testing.assert_array_equal(got, cur)
+        assert counts == want_counts
+        got2, counts2 = oracle_mod.fnr_passes(a, k, 3, threads=4)
+        np.testing.assert_array_equal(got2, cur)
+        assert counts2 == counts
+
+
 def test_pitched_input(oracle_mod):
     rng = np.random.default_rng(5)
     a = rng.integers(0, 65536, (11, 13)).astype(np.uint16)
