@@ -188,37 +188,40 @@ __device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW,
 }
 
 // TMA fills out-of-frame cells with zero. A warp replaces, in the stage rows
-// [row0, row1) it is about to read, every out-of-frame cell by the nearest
-// in-frame one: first the in-frame columns of out-of-frame rows (copied from
-// the nearest in-frame row), then the out-of-frame columns of every row (from
-// the row's own edge cell). Several warps may patch the same cell; every
-// write stores that cell's final value, so the overlap is harmless.
+// [row0, row1) it is about to read, every out-of-frame cell that a window
+// reads (columns [cmin, cmax]) by the nearest in-frame one: first the
+// in-frame columns of out-of-frame rows (copied from the nearest in-frame
+// row), then the out-of-frame columns of every row (from the row's own edge
+// cell). Several warps may patch the same cell; every write stores that
+// cell's final value, so the overlap is harmless.
 template <typename T>
-__device__ void fixup_rows_warp(T *S, int xs, int ys, int BW, int W, int H, int row0, int row1, int lane) {
+__device__ void fixup_rows_warp(T *S, int xs, int ys, int BW, int W, int H, int row0, int row1, int cmin, int cmax,
+                                int lane) {
   const int top = -ys, bot = H - 1 - ys;     // stage rows of frame rows 0 and H-1
   const int lft = -xs, rgt = W - 1 - xs;     // stage columns of frame columns 0 and W-1
-  const int c0 = lft > 0 ? lft : 0;
-  const int c1 = rgt < BW - 1 ? rgt : BW - 1;
+  const int c0 = lft > cmin ? lft : cmin;
+  const int c1 = rgt < cmax ? rgt : cmax;
   for (int row = row0; row < row1; ++row) {
     const int src = row < top ? top : (row > bot ? bot : row);
     if (src != row)
       for (int c = c0 + lane; c <= c1; c += 32) S[row * BW + c] = S[src * BW + c];
   }
   __syncwarp();
-  if (lft > 0 || rgt < BW - 1) {
+  if (lft > cmin || rgt < cmax) {
     for (int row = row0 + lane; row < row1; row += 32) {
       T *Rw = S + row * BW;
-      if (lft > 0) {
+      if (lft > cmin) {
         const T v = Rw[lft];
-        for (int j = 0; j < lft; ++j) Rw[j] = v;
+        for (int j = cmin; j < lft; ++j) Rw[j] = v;
       }
-      if (rgt < BW - 1) {
+      if (rgt < cmax) {
         const T v = Rw[rgt];
-        for (int j = rgt + 1; j < BW; ++j) Rw[j] = v;
+        for (int j = rgt + 1; j <= cmax; ++j) Rw[j] = v;
       }
     }
   }
   __syncwarp();
+  (void)BW;
 }
 
 // Plain store of output rows [r0, r0+rows) of the tile (frame-clipped).
@@ -602,13 +605,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   const int TW = p.tile_w, TH = p.tile_h;
   const Layout L = make_layout(E, K, ALGO, TH, TW);
   const int BW = L.bw, BH = L.bh, SR = L.sr;
+  constexpr int NS = num_stages(ALGO);
   const uint32_t box_bytes = static_cast<uint32_t>(BW * BH * E);
-  T *const stage0 = reinterpret_cast<T *>(smem + L.off_stage[0]);
-  T *const stage1 = reinterpret_cast<T *>(smem + L.off_stage[1]);
+  const int stage_stride = L.off_stage[1] - L.off_stage[0];
+  auto stage_ptr = [&](int s) { return reinterpret_cast<T *>(smem + L.off_stage[0] + s * stage_stride); };
   T *const out0 = reinterpret_cast<T *>(smem + L.off_out[0]);
   T *const out1 = reinterpret_cast<T *>(smem + L.off_out[1]);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bar);  // [2]: tile staged
-  uint64_t *empty = full + 2;                                        // [2]: all consumers done with it
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bar);  // [NS]: tile staged
+  uint64_t *empty = full + NS;                                       // [NS]: all consumers done with it
   TileInfo *info = reinterpret_cast<TileInfo *>(smem + L.off_info);  // [stage]: tile staged there
   int *dir = reinterpret_cast<int *>(smem + L.off_dir);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -616,10 +620,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   if (p.table != nullptr && p.nframes <= kDirMax)
     for (int f = tid; f < p.nframes; f += kThreads) dir[f] = p.table[f].tile_begin;
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], kConsumerWarps);
-    mbar_init(&empty[1], kConsumerWarps);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
     fence_mbar_init();
     if (blockIdx.x == 0 && p.launches != nullptr) atomicAdd(p.launches, 1ull);
   }
@@ -628,13 +632,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------- producer
     for (int i = 0;; ++i) {
-      const int s = i & 1;
-      if (i >= 2 && !mbar_wait_bounded(&empty[s], ((i >> 1) - 1) & 1u, kWaitCycles)) {
+      const int s = i % NS, use = i / NS;
+      // the stage's previous tile (i - NS) must be released by every consumer warp
+      if (use >= 1 && !mbar_wait_bounded(&empty[s], (use - 1) & 1u, kWaitCycles)) {
         if (lane == 0) atomicOr(p.status, kStatusTimeout);
         break;
       }
       const TileInfo ti = locate_tile(p, dir, blockIdx.x + i * static_cast<int>(gridDim.x));
-      T *const S = s ? stage1 : stage0;
+      T *const S = stage_ptr(s);
       if (lane == 0) info[s] = ti;
       if (!ti.valid) {
         __syncwarp();
@@ -664,8 +669,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   const int seg_shift = 31 - __clz(TW >> 3);  // dense 3x3: tile_w / 8 is a power of two
   unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;
   for (int i = 0;; ++i) {
-    const int s = i & 1;
-    if (!mbar_wait_bounded(&full[s], (i >> 1) & 1u, kWaitCycles)) {
+    const int s = i % NS;
+    if (!mbar_wait_bounded(&full[s], (i / NS) & 1u, kWaitCycles)) {
       if (lane == 0) atomicOr(p.status, kStatusTimeout);
       break;
     }
@@ -680,13 +685,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     // touch the bytes between W and the pitch: such tiles use plain stores.
     const bool ragged_right = x0 + TW > cur.W && ((cur.W * E) & 15) != 0;
     const bool tma_out = (cur.flags & kFrameTmaOut) != 0 && !ragged_right;
-    T *const S = s ? stage1 : stage0;
-    T *const O = s ? out1 : out0;
+    T *const S = stage_ptr(s);
+    T *const O = (i & 1) ? out1 : out0;  // output tiles alternate independently of the stage ring
     const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
     if (live && ALGO == ALGO_DENSE3) {
-      if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
-        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, lane);
+      if (tma_in && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, lane);
       // results go straight from registers to the frame (no output tile)
       const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
@@ -707,8 +712,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
                                       lane, flagged);
       }
     } else if (live) {
-      if (tma_in && (xs < 0 || ys < 0 || xs + BW > cur.W || ys + BH > cur.H))
-        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, lane);
+      if (tma_in && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, lane);
       if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
       __syncwarp();
       int flagged = 0;

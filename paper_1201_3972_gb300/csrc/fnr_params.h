@@ -59,6 +59,11 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
   return align_up(r, 16 / esize);
 }
 
+// Staging buffers per CTA (a ring: the producer loads up to this many tiles
+// ahead of the slowest consumer warp).
+__host__ __device__ constexpr int num_stages(int algo) { return algo == ALGO_DENSE3 ? 3 : 2; }
+constexpr int kMaxStages = 3;
+
 // Rows per vertical/horizontal extreme group of the compacted strategies.
 __host__ __device__ constexpr int row_group(int k) { return k >= 8 ? 8 : (k >= 4 ? 4 : 2); }
 
@@ -73,13 +78,13 @@ __host__ __device__ constexpr int tile_h_multiple(int k, int algo) {
 // flagged list, vertical extremes and (bit-plane strategy) bit planes.
 struct Layout {
   int r, bw, bh, vw, pw, nbmax, sr;
-  int off_stage[2];
+  int off_stage[kMaxStages];
   int off_out[2];
   int off_warp;        // first per-warp block
   int warp_bytes;      // size of one per-warp block
   int w_list, w_vmin, w_vmax, w_planes;  // offsets inside a per-warp block
   int plane_rows;      // rows of bit planes a warp builds (its strip + halo)
-  int off_bar;         // full[2], empty[2]
+  int off_bar;         // full[stages], empty[stages]
   int off_info;
   int off_dir;
   int total;
@@ -100,8 +105,10 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   const int stage = align_up(L.bw * L.bh * esize, 128);
   // the dense 3x3 strategy writes results straight from registers: no output tile
   const int outb = algo == ALGO_DENSE3 ? 0 : align_up(tile_w * tile_h * esize, 128);
-  L.off_stage[0] = off; off += stage;
-  L.off_stage[1] = off; off += stage;
+  for (int i = 0; i < kMaxStages; ++i) {
+    L.off_stage[i] = off;
+    if (i < num_stages(algo)) off += stage;
+  }
   L.off_out[0] = off; off += outb;
   L.off_out[1] = off; off += outb;
   L.w_list = L.w_vmin = L.w_vmax = L.w_planes = -1;
@@ -116,8 +123,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   }
   L.warp_bytes = align_up(w, 128);
   L.off_warp = off; off += kConsumerWarps * L.warp_bytes;
-  L.off_bar = off; off += 32;
-  L.off_info = off; off += 64;
+  L.off_bar = off; off += 16 * kMaxStages;
+  L.off_info = off; off += 32 * kMaxStages;
   L.off_dir = off; off += kDirMax * 4;
   L.total = align_up(off, 128);
   return L;
