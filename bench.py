@@ -39,6 +39,24 @@ UNIT = "Mpixel/s"
 WORKLOAD = "640x512 14-bit sweep: salt-and-pepper 5/10/20/40%, windows 3/5/7"
 
 
+def recorded_traffic(k: str, frames: int):
+    """DRAM bytes per launch of the class-k kernel from the committed ncu record,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_sweep_640x512_u14.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha1()
+    for src in rec["kernel_sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["kernel_sources_sha1"] or k not in rec["bytes_per_frame"]:
+        return None
+    return int(rec["bytes_per_frame"][k]) * frames
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -255,7 +273,8 @@ def own_arm(args):
     dom = per_k[dom_k]
     roofline = {"bound": "hbm", "kernel": f"fnr_kernel k={dom_k} u16 ({_lib.ALGO_NAMES[dom['config']['algo']]})",
                 "achieved": round(dom["achieved_gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(dom["achieved_gbs"] / hbm_peak, 4), "traffic": None,
+                "frac": round(dom["achieved_gbs"] / hbm_peak, 4),
+                "traffic": recorded_traffic(dom_k, dom["frames"]),
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
 
     result = {
