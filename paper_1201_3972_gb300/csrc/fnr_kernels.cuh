@@ -410,66 +410,162 @@ __device__ __forceinline__ void sliding_extreme(const uint32_t (&v)[RG + K - 1],
   }
 }
 
-// Vertical pass over the strip: vmin/vmax[q][j] = min/max of stage column
-// (XOFF-R+j) over stage rows r0+q .. r0+q+K-1, q < SR, j < VW.
+// Fast exact division by a runtime divisor d >= 1 for dividends below 2^16:
+// q = umulhi(n, ceil(2^32 / d)); d = 1 (whose multiplier 2^32 does not fit in
+// 32 bits) returns n itself.
+struct FastDiv {
+  uint32_t m;
+  bool one;
+  __device__ explicit FastDiv(uint32_t d)
+      : m(d > 1 ? static_cast<uint32_t>((0xffffffffull + d) / d) : 0u), one(d <= 1) {}
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return one ? n : __umulhi(n, m); }
+};
+
+// Pair word of stage row `row` at even stage column `col`: pixels (col, col+1)
+// in the low and high 16-bit lanes.
+template <typename T>
+__device__ __forceinline__ uint32_t pair_word(const T *S, int row, int BW, int col);
+
+template <>
+__device__ __forceinline__ uint32_t pair_word<uint16_t>(const uint16_t *S, int row, int BW, int col) {
+  return *reinterpret_cast<const uint32_t *>(S + row * BW + col);
+}
+
+template <>
+__device__ __forceinline__ uint32_t pair_word<uint8_t>(const uint8_t *S, int row, int BW, int col) {
+  return __byte_perm(static_cast<uint32_t>(*reinterpret_cast<const uint16_t *>(S + row * BW + col)), 0, 0x4140);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(T *O, int idx, uint32_t w);
+
+template <>
+__device__ __forceinline__ void store_pair<uint16_t>(uint16_t *O, int idx, uint32_t w) {
+  *reinterpret_cast<uint32_t *>(O + idx) = w;
+}
+
+template <>
+__device__ __forceinline__ void store_pair<uint8_t>(uint8_t *O, int idx, uint32_t w) {
+  *reinterpret_cast<uint16_t *>(O + idx) = static_cast<uint16_t>(__byte_perm(w, 0, 0x0020));
+}
+
+// Sliding packed extreme (min.u16x2 / max.u16x2) over windows [q, q+K-1] of
+// RG+K-1 words, sharing the core [RG-1, K-1] common to all windows (RG <= K).
+template <int K, int RG, bool MAX>
+__device__ __forceinline__ void sliding_extreme2(const uint32_t (&v)[RG + K - 1], uint32_t (&out)[RG]) {
+  auto op = [](uint32_t a, uint32_t b) { return MAX ? vmax2(a, b) : vmin2(a, b); };
+  uint32_t core = v[RG - 1];
+#pragma unroll
+  for (int i = RG; i <= K - 1; ++i) core = op(core, v[i]);
+  uint32_t suf[RG], pre[RG];
+  if constexpr (RG >= 2) {
+    suf[RG - 2] = v[RG - 2];
+#pragma unroll
+    for (int q = RG - 3; q >= 0; --q) suf[q] = op(v[q], suf[q + 1]);
+    pre[1] = v[K];
+#pragma unroll
+    for (int q = 2; q < RG; ++q) pre[q] = op(pre[q - 1], v[K - 1 + q]);
+  }
+#pragma unroll
+  for (int q = 0; q < RG; ++q) {
+    uint32_t a = core;
+    if (q <= RG - 2) a = op(a, suf[q]);
+    if (q >= 1) a = op(a, pre[q]);
+    out[q] = a;
+  }
+}
+
+// Vertical pass over the strip on column pairs: vminP/vmaxP[q][p] = packed
+// min/max of stage columns (cb + 2p, cb + 2p + 1) over stage rows
+// r0+q .. r0+q+K-1, q < SR, p < NP.
 template <typename T, int K>
-__device__ void vertical_strip(const T *S, uint16_t *vmin, uint16_t *vmax, int BW, int VW, int r0, int SR, int lane) {
-  constexpr int R = (K - 1) / 2, RG = row_group(K);
-  constexpr int XOFF = xoff_for(R, sizeof(T));
-  const int items = VW * (SR / RG);
+__device__ void vertical_pairs(const T *S, uint32_t *vminP, uint32_t *vmaxP, int BW, int NP, int cb, int r0, int SR,
+                               const FastDiv &divNP, int lane) {
+  constexpr int RG = row_group(K);
+  const int items = NP * (SR / RG);
   for (int it = lane; it < items; it += 32) {
-    const int g = it / VW, j = it - g * VW;
-    const T *col = S + (r0 + g * RG) * BW + (XOFF - R) + j;
+    const int g = static_cast<int>(divNP.div(static_cast<uint32_t>(it))), p = it - g * NP;
+    const int col = cb + 2 * p, row0 = r0 + g * RG;
     uint32_t v[RG + K - 1];
 #pragma unroll
-    for (int i = 0; i < RG + K - 1; ++i) v[i] = col[i * BW];
+    for (int i = 0; i < RG + K - 1; ++i) v[i] = pair_word<T>(S, row0 + i, BW, col);
     uint32_t mn[RG], mx[RG];
-    sliding_extreme<K, RG, false>(v, mn);
-    sliding_extreme<K, RG, true>(v, mx);
+    sliding_extreme2<K, RG, false>(v, mn);
+    sliding_extreme2<K, RG, true>(v, mx);
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
-      vmin[(g * RG + q) * VW + j] = static_cast<uint16_t>(mn[q]);
-      vmax[(g * RG + q) * VW + j] = static_cast<uint16_t>(mx[q]);
+      vminP[(g * RG + q) * NP + p] = mn[q];
+      vmaxP[(g * RG + q) * NP + p] = mx[q];
     }
   }
 }
 
-// Horizontal pass + flag over the strip: every centre value goes to the
-// output tile; flagged in-frame pixels are appended to the warp's list as
-// (row in strip << 8 | column). Returns the list length (warp-uniform).
+// Horizontal pass + flag over the strip, PPI output pairs (2*PPI pixels) per
+// lane item: every centre value goes to the output tile; flagged in-frame
+// pixels (all in-frame pixels when `all`) are appended to the warp's list as
+// (row in strip << 8 | column). The window of output column x spans stage
+// columns XOFF+x-R .. XOFF+x+R; for a pair (x, x+1) the packed window term at
+// offset d is the pair word at stage column XOFF+x+d, which is a byte permute
+// of two stored words when that column is odd relative to cb (compile time).
+// Returns the list length (warp-uniform).
 template <typename T, int K>
-__device__ int horizontal_flag_strip(const T *S, const uint16_t *vmin, const uint16_t *vmax, T *O, uint16_t *list,
-                                     int TW, int BW, int VW, int r0, int SR, int tw_valid, int th_valid, bool all,
-                                     int lane) {
-  constexpr int R = (K - 1) / 2, RG = row_group(K);
+__device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_t *vmaxP, T *O, uint16_t *list, int TW,
+                                int BW, int NP, int r0, int SR, int tw_valid, int th_valid, bool all,
+                                const FastDiv &divG, int lane) {
+  constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
-  const int per_row = TW / RG;
-  const int items = SR * per_row;
+  constexpr int CB = (XOFF - R) & ~1;
+  constexpr int OFF0 = XOFF - CB;          // stage column XOFF relative to CB
+  constexpr int PPI = 4;                   // output pairs per item
+  constexpr int W0 = (OFF0 - R) >> 1;      // first word an item reads, relative to 2*pair index / 2
+  constexpr int NW = ((OFF0 + 2 * PPI - 1 + R) >> 1) - W0 + 1;
+  const int gpr = TW / (2 * PPI);          // items per row
+  const int items = SR * gpr;
   int base = 0;
   for (int it0 = 0; it0 < items; it0 += 32) {
     const int it = it0 + lane;
     uint32_t fm = 0;
-    int q0 = 0, tx0 = 0;
+    int q = 0, x0p = 0;
     if (it < items) {
-      q0 = it / per_row;
-      tx0 = (it - q0 * per_row) * RG;
-      uint32_t hmn[RG + K - 1], hmx[RG + K - 1];
+      q = static_cast<int>(divG.div(static_cast<uint32_t>(it)));
+      const int grp = it - q * gpr;
+      x0p = grp * 2 * PPI;                 // first output column of the item (tile coordinates)
+      const int wbase = (x0p >> 1) + W0;   // = (OFF0 + x0p - R) >> 1 since x0p is even
+      uint32_t mnw[NW], mxw[NW];
 #pragma unroll
-      for (int i = 0; i < RG + K - 1; ++i) {
-        hmn[i] = vmin[q0 * VW + tx0 + i];
-        hmx[i] = vmax[q0 * VW + tx0 + i];
+      for (int i = 0; i < NW; ++i) {
+        mnw[i] = vminP[q * NP + wbase + i];
+        mxw[i] = vmaxP[q * NP + wbase + i];
       }
-      uint32_t gmin[RG], gmax[RG];
-      sliding_extreme<K, RG, false>(hmn, gmin);
-      sliding_extreme<K, RG, true>(hmx, gmax);
-      const int ty = r0 + q0;
-      const T *crow = S + (ty + R) * BW + XOFF + tx0;
+      const int ty = r0 + q;
 #pragma unroll
-      for (int q = 0; q < RG; ++q) {
-        const uint32_t c = crow[q];
-        O[ty * TW + tx0 + q] = static_cast<T>(c);
-        const bool inside = ty < th_valid && tx0 + q < tw_valid;
-        fm |= static_cast<uint32_t>(inside && (all || c == gmin[q] || c == gmax[q])) << q;
+      for (int j = 0; j < PPI; ++j) {
+        uint32_t gmin = 0xffffffffu, gmax = 0u;
+#pragma unroll
+        for (int d = -R; d <= R; ++d) {
+          constexpr int dummy = 0;
+          (void)dummy;
+          const int col = OFF0 + 2 * j + d;  // relative to x0p, plus OFF0 (compile time)
+          const int w = (col >> 1) - W0;
+          uint32_t a, b;
+          if (col & 1) {
+            a = __byte_perm(mnw[w], mnw[w + 1], 0x5432);
+            b = __byte_perm(mxw[w], mxw[w + 1], 0x5432);
+          } else {
+            a = mnw[w];
+            b = mxw[w];
+          }
+          gmin = d == -R ? a : vmin2(gmin, a);
+          gmax = d == -R ? b : vmax2(gmax, b);
+        }
+        const int x = x0p + 2 * j;
+        const uint32_t c = pair_word<T>(S, ty + R, BW, XOFF + x);
+        store_pair<T>(O, ty * TW + x, c);
+        const uint32_t z = vmin2(c - gmin, gmax - c);  // a zero lane: c equals an extreme
+        const bool in_row = ty < th_valid;
+        const bool f0 = in_row && x < tw_valid && (all || (z & 0xffffu) == 0);
+        const bool f1 = in_row && x + 1 < tw_valid && (all || (z >> 16) == 0);
+        fm |= (static_cast<uint32_t>(f0) | (static_cast<uint32_t>(f1) << 1)) << (2 * j);
       }
     }
     const int cnt = __popc(fm);
@@ -480,9 +576,11 @@ __device__ int horizontal_flag_strip(const T *S, const uint16_t *vmin, const uin
       if (lane >= o) incl += y;
     }
     int pos = base + incl - cnt;
-#pragma unroll
-    for (int q = 0; q < RG; ++q)
-      if ((fm >> q) & 1u) list[pos++] = static_cast<uint16_t>((q0 << 8) | (tx0 + q));
+    while (fm) {
+      const int bit = __ffs(fm) - 1;
+      fm &= fm - 1;
+      list[pos++] = static_cast<uint16_t>((q << 8) | (x0p + bit));
+    }
     base += __shfl_sync(0xffffffffu, incl, 31);
   }
   __syncwarp();
@@ -667,6 +765,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   // --------------------------------------------------------------- consumers
   const int r0 = warp * SR;  // this warp's output rows [r0, r0 + SR)
   const int seg_shift = 31 - __clz(TW >> 3);  // dense 3x3: tile_w / 8 is a power of two
+  const FastDiv divNP(static_cast<uint32_t>(L.np));     // compacted: vertical items per row group
+  const FastDiv divG(static_cast<uint32_t>(TW / 8));    // compacted: horizontal items per row
   unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;
   for (int i = 0;; ++i) {
     const int s = i % NS;
@@ -719,12 +819,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       int flagged = 0;
       {
         uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
-        uint16_t *vmin = reinterpret_cast<uint16_t *>(wbase + L.w_vmin);
-        uint16_t *vmax = reinterpret_cast<uint16_t *>(wbase + L.w_vmax);
-        vertical_strip<T, K>(S, vmin, vmax, BW, L.vw, r0, SR, lane);
+        uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
+        uint32_t *vmax = reinterpret_cast<uint32_t *>(wbase + L.w_vmax);
+        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.cb, r0, SR, divNP, lane);
         __syncwarp();
-        flagged = horizontal_flag_strip<T, K>(S, vmin, vmax, O, list, TW, BW, L.vw, r0, SR, cur.W - x0, cur.H - y0,
-                                              p.mode == kModeMedian, lane);
+        flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.np, r0, SR, cur.W - x0, cur.H - y0,
+                                         p.mode == kModeMedian, divG, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {

@@ -78,6 +78,7 @@ __host__ __device__ constexpr int tile_h_multiple(int k, int algo) {
 // flagged list, vertical extremes and (bit-plane strategy) bit planes.
 struct Layout {
   int r, bw, bh, vw, pw, nbmax, sr;
+  int cb, np;          // packed column pairs: first stage column (even) and words per row
   int off_stage[kMaxStages];
   int off_out[2];
   int off_warp;        // first per-warp block
@@ -97,12 +98,16 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   L.bw = tile_w + 2 * xoff;
   L.bh = tile_h + 2 * L.r;
   L.vw = tile_w + 2 * L.r;
+  // pair words cover stage columns [cb, cb + 2 np): every column a window reads
+  L.cb = (xoff - L.r) & ~1;
+  L.np = (xoff + tile_w + L.r - 1 - L.cb) / 2 + 1;
   L.pw = (L.bw + 31) / 32 + 1;
   L.nbmax = 8 * esize;
   L.sr = tile_h / kConsumerWarps;
   L.plane_rows = L.sr + k - 1;
   int off = 0;
-  const int stage = align_up(L.bw * L.bh * esize, 128);
+  // +16: a pair word may read one pixel past the last staged column (never used)
+  const int stage = align_up(L.bw * L.bh * esize + 16, 128);
   // the dense 3x3 strategy writes results straight from registers: no output tile
   const int outb = algo == ALGO_DENSE3 ? 0 : align_up(tile_w * tile_h * esize, 128);
   for (int i = 0; i < kMaxStages; ++i) {
@@ -115,8 +120,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   int w = 0;
   if (algo != ALGO_DENSE3) {
     L.w_list = w; w += align_up(L.sr * tile_w * 2, 16);
-    L.w_vmin = w; w += align_up(L.sr * L.vw * 2, 16);
-    L.w_vmax = w; w += align_up(L.sr * L.vw * 2, 16);
+    L.w_vmin = w; w += align_up(L.sr * L.np * 4, 16);
+    L.w_vmax = w; w += align_up(L.sr * L.np * 4, 16);
   }
   if (algo == ALGO_BITPLANE) {
     L.w_planes = w; w += align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);
