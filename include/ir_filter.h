@@ -62,6 +62,15 @@ typedef enum {
   IR_ALGO_BITPLANE = 3       /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
 } ir_algo;
 
+/* How windows read pixels outside the frame. The paper does not say; every
+ * pixel, border included, gets a full k x k window (Table 1 evaluates all
+ * 364 x 244 pixels), so the default replicates the nearest edge pixel. */
+typedef enum {
+  IR_BORDER_REPLICATE = 0,   /* clamp to the nearest edge pixel (default) */
+  IR_BORDER_MIRROR = 1,      /* reflect about the edge pixel: d c b | a b c d | c b a */
+  IR_BORDER_ZERO = 2         /* outside pixels read as 0 */
+} ir_border;
+
 /* Kernel configuration for one (dtype, k) class. tile_w, tile_h: output tile
  * in pixels (multiples of 8; tile_w + halo <= 256 pixels). ctas_per_sm: 0 = as
  * many as fit. */
@@ -162,6 +171,12 @@ ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pitch_bytes, i
 /* Read and clear the handle's device status word (synchronises the device).
  * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call. */
 ir_status ir_filter_sync_status(ir_filter *h);
+
+/* Border reading for the handle's later calls (single frames, passes, median
+ * filter, batch plans created afterwards). IR_EINVAL for an unknown mode.
+ * ir_filter_run_noalloc and the server always replicate. */
+ir_status ir_filter_set_border(ir_filter *h, ir_border mode);
+ir_border ir_filter_get_border(const ir_filter *h);
 
 /* Tuning. ir_filter_autotune times every built candidate for (dtype, k) on a
  * synthetic H x W frame on `cuda_stream` and keeps the fastest; the table is

@@ -49,6 +49,8 @@ def _load():
         lib.oracle_fnr_mt.restype = ll
         lib.oracle_fnr_stack.argtypes = [vp, vp, ll, i32, i32, i32, i32, i32]
         lib.oracle_fnr_stack.restype = ll
+        lib.oracle_fnr_border.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32, i32]
+        lib.oracle_fnr_border.restype = ll
         lib.oracle_median_filter.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32]
         lib.oracle_median_filter.restype = ll
         lib.oracle_introsort.argtypes = [vp, ctypes.c_long, i32]
@@ -77,6 +79,23 @@ def fnr(frame: np.ndarray, k: int):
                        H, W, es, int(k))
     if f < 0:
         raise ValueError(f"oracle rejected arguments (H={H}, W={W}, k={k})")
+    return out, int(f)
+
+
+BORDERS = {"replicate": 0, "mirror": 1, "zero": 2}
+
+
+def fnr_border(frame: np.ndarray, k: int, border: str):
+    """FNR with a border reading: "replicate" (default elsewhere), "mirror"
+    (reflect without repeating the edge pixel) or "zero"."""
+    lib = _load()
+    es = _check_frame(frame)
+    out = np.empty(frame.shape, dtype=frame.dtype)
+    H, W = frame.shape
+    f = lib.oracle_fnr_border(frame.ctypes.data, frame.strides[0], out.ctypes.data, out.strides[0],
+                              H, W, es, int(k), BORDERS[border])
+    if f < 0:
+        raise ValueError("oracle rejected arguments")
     return out, int(f)
 
 

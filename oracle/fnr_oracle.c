@@ -142,10 +142,41 @@ static void store_px(unsigned char *base, long long pitch, int esize, int y, int
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* Border readings (the paper is silent; replicate is the default):
+ *   0 replicate: clamp to the nearest edge pixel;
+ *   1 mirror: reflect about the edge pixel without repeating it (d c b | a b c d | c b a),
+ *     periodic with period 2(n-1) for windows wider than the frame;
+ *   2 zero: pixels outside the frame read as 0.
+ * Returns the in-frame index to read, or -1 for "reads 0". */
+static int border_index(int i, int n, int mode)
+{
+    if (i >= 0 && i < n) return i;
+    if (mode == 2) return -1;
+    if (mode == 1) {
+        if (n == 1) return 0;
+        int period = 2 * (n - 1);
+        int j = i % period;
+        if (j < 0) j += period;
+        return j < n ? j : period - j;
+    }
+    return clampi(i, 0, n - 1);
+}
+
 /* Rows [y0, y1) of the output. w is scratch for n = k*k values. */
+static long long fnr_rows_b(const unsigned char *in, long long in_pitch,
+                            unsigned char *out, long long out_pitch,
+                            int H, int W, int esize, int k, int y0, int y1, uint32_t *w, int border);
+
 static long long fnr_rows(const unsigned char *in, long long in_pitch,
                           unsigned char *out, long long out_pitch,
                           int H, int W, int esize, int k, int y0, int y1, uint32_t *w)
+{
+    return fnr_rows_b(in, in_pitch, out, out_pitch, H, W, esize, k, y0, y1, w, 0);
+}
+
+static long long fnr_rows_b(const unsigned char *in, long long in_pitch,
+                            unsigned char *out, long long out_pitch,
+                            int H, int W, int esize, int k, int y0, int y1, uint32_t *w, int border)
 {
     const int r = (k - 1) / 2;
     const int n = k * k;
@@ -153,13 +184,13 @@ static long long fnr_rows(const unsigned char *in, long long in_pitch,
     long long flagged = 0;
     for (int y = y0; y < y1; y++) {
         for (int x = 0; x < W; x++) {
-            /* 1. S_xy, centre included, row-major, replicate border */
+            /* 1. S_xy, centre included, row-major, border per the reading in use */
             int i = 0;
             for (int dy = -r; dy <= r; dy++) {
-                int yy = clampi(y + dy, 0, H - 1);
+                int yy = border_index(y + dy, H, border);
                 for (int dx = -r; dx <= r; dx++) {
-                    int xx = clampi(x + dx, 0, W - 1);
-                    w[i++] = load_px(in, in_pitch, esize, yy, xx);
+                    int xx = border_index(x + dx, W, border);
+                    w[i++] = (yy < 0 || xx < 0) ? 0u : load_px(in, in_pitch, esize, yy, xx);
                 }
             }
             /* 2. g_max and g_min (Eq. 3a, 3b) */
@@ -205,6 +236,19 @@ long long oracle_fnr(const void *in, long long in_pitch, void *out, long long ou
     if (!w) return -1;
     long long f = fnr_rows((const unsigned char *)in, in_pitch, (unsigned char *)out, out_pitch,
                            H, W, esize, k, 0, H, w);
+    free(w);
+    return f;
+}
+
+/* oracle_fnr with a border reading other than replicate (see border_index). */
+long long oracle_fnr_border(const void *in, long long in_pitch, void *out, long long out_pitch,
+                            int H, int W, int esize, int k, int border)
+{
+    if (!args_ok(in, in_pitch, out, out_pitch, H, W, esize, k) || border < 0 || border > 2) return -1;
+    uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)k * (size_t)k);
+    if (!w) return -1;
+    long long f = fnr_rows_b((const unsigned char *)in, in_pitch, (unsigned char *)out, out_pitch,
+                             H, W, esize, k, 0, H, w, border);
     free(w);
     return f;
 }

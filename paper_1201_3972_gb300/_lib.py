@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(PKG, "libirfnr.so")
 IR_OK, IR_EINVAL, IR_EALIGN, IR_ENOMEM, IR_ECUDA, IR_ETIMEOUT, IR_EBUSY, IR_EUNSUPPORTED = range(8)
 IR_U8, IR_U16, IR_U14 = 0, 1, 2
 IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE = 0, 1, 2, 3
+IR_BORDER_REPLICATE, IR_BORDER_MIRROR, IR_BORDER_ZERO = 0, 1, 2
+BORDER_CODES = {"replicate": IR_BORDER_REPLICATE, "mirror": IR_BORDER_MIRROR, "zero": IR_BORDER_ZERO}
 ALGO_NAMES = {IR_ALGO_AUTO: "auto", IR_ALGO_DENSE3: "dense3", IR_ALGO_NETWORK: "network",
               IR_ALGO_BITPLANE: "bitplane"}
 
@@ -27,7 +29,8 @@ EXPORTED = (
     "ir_batch_plan_create", "ir_batch_plan_launch", "ir_batch_plan_kernel_count", "ir_batch_plan_destroy",
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
-    "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes",
+    "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
+    "ir_filter_get_border",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
     "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
@@ -113,6 +116,8 @@ def load(path: Optional[str] = None):
             "ir_filter_version": ([], ctypes.c_char_p),
             "ir_filter_run_noalloc": ([vp, i32, i32, sz, i32, i32, vp], i32),
             "ir_filter_median_filter": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
+            "ir_filter_set_border": ([vp, i32], i32),
+            "ir_filter_get_border": ([vp], i32),
             "ir_filter_run_passes": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, i32, vp, vp], i32),
             "ir_server_create": ([i32, ctypes.POINTER(ir_server_config), ctypes.POINTER(vp)], i32),
             "ir_server_destroy": ([vp], None),
@@ -230,6 +235,14 @@ class Filter:
         _check(self.lib, self.h, self.lib.ir_filter_run_passes(self.h, _ptr(src), in_pitch, _ptr(dst), out_pitch, H,
                                                                W, dtype, k, passes, _stream(stream),
                                                                _ptr(flagged_per_pass) or None))
+
+    def set_border(self, border) -> None:
+        """Border reading for later calls: "replicate" (default), "mirror" or "zero"."""
+        code = BORDER_CODES[border] if isinstance(border, str) else int(border)
+        _check(self.lib, self.h, self.lib.ir_filter_set_border(self.h, code))
+
+    def get_border(self) -> int:
+        return int(self.lib.ir_filter_get_border(self.h))
 
     def median_filter(self, src, dst, k: int, u14: bool = False, stream=None, median_count=None) -> None:
         """Standard median filter (every pixel), the paper's MF baseline."""

@@ -171,53 +171,66 @@ __device__ __forceinline__ T load_global(const unsigned char *base, long long pi
   return __ldg(reinterpret_cast<const T *>(base + (long long)y * pitch) + x);
 }
 
-// Plain staging by one warp for frames TMA cannot address: clamped
-// coordinates give the replicated border directly.
+// In-frame index that frame coordinate i (frame size n) reads under a border
+// reading, or -1 when it reads 0 (zero border). Mirror reflects about the
+// edge pixel and repeats with period 2(n-1) for offsets wider than the frame.
+__device__ __forceinline__ int border_src(int i, int n, int border) {
+  if (i >= 0 && i < n) return i;
+  if (border == kBorderZero) return -1;
+  if (border == kBorderMirror) {
+    if (n == 1) return 0;
+    const int period = 2 * (n - 1);
+    int j = i % period;
+    j = j < 0 ? j + period : j;
+    return j < n ? j : period - j;
+  }
+  return i < 0 ? 0 : n - 1;
+}
+
+// Plain staging by one warp for frames TMA cannot address: the border
+// mapping gives the out-of-frame cells directly.
 template <typename T>
-__device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW, int BH, int lane) {
+__device__ void plain_tile_load(const FrameDev *f, int xs, int ys, T *S, int BW, int BH, int border, int lane) {
   const int H = f->H, W = f->W;
   for (int row = 0; row < BH; ++row) {
-    int gy = ys + row;
-    gy = gy < 0 ? 0 : (gy >= H ? H - 1 : gy);
+    const int gy = border_src(ys + row, H, border);
     for (int col = lane; col < BW; col += 32) {
-      int gx = xs + col;
-      gx = gx < 0 ? 0 : (gx >= W ? W - 1 : gx);
-      S[row * BW + col] = load_global<T>(f->in, f->in_pitch, gy, gx);
+      const int gx = border_src(xs + col, W, border);
+      S[row * BW + col] = (gy < 0 || gx < 0) ? T(0) : load_global<T>(f->in, f->in_pitch, gy, gx);
     }
   }
 }
 
-// TMA fills out-of-frame cells with zero. A warp replaces, in the stage rows
-// [row0, row1) it is about to read, every out-of-frame cell that a window
-// reads (columns [cmin, cmax]) by the nearest in-frame one: first the
-// in-frame columns of out-of-frame rows (copied from the nearest in-frame
-// row), then the out-of-frame columns of every row (from the row's own edge
-// cell). Several warps may patch the same cell; every write stores that
-// cell's final value, so the overlap is harmless.
+// TMA fills out-of-frame cells with zero (already right for the zero
+// border). For replicate and mirror a warp rewrites, in the stage rows
+// [row0, row1) it is about to read, every out-of-frame cell that a window of
+// an in-frame pixel reads (columns [cmin, cmax], frame rows and columns
+// within R of the frame) with the in-frame pixel the border reading maps it
+// to: first the in-frame columns of out-of-frame rows (copied from the mapped
+// row), then the out-of-frame columns of every row (from the mapped column of
+// the same row). Several warps may patch the same cell; every write stores
+// that cell's final value, so the overlap is harmless.
 template <typename T>
 __device__ void fixup_rows_warp(T *S, int xs, int ys, int BW, int W, int H, int row0, int row1, int cmin, int cmax,
-                                int lane) {
-  const int top = -ys, bot = H - 1 - ys;     // stage rows of frame rows 0 and H-1
+                                int R, int border, int lane) {
   const int lft = -xs, rgt = W - 1 - xs;     // stage columns of frame columns 0 and W-1
   const int c0 = lft > cmin ? lft : cmin;
   const int c1 = rgt < cmax ? rgt : cmax;
   for (int row = row0; row < row1; ++row) {
-    const int src = row < top ? top : (row > bot ? bot : row);
-    if (src != row)
-      for (int c = c0 + lane; c <= c1; c += 32) S[row * BW + c] = S[src * BW + c];
+    const int gy = ys + row;
+    if (gy >= 0 && gy < H) continue;
+    if (gy < -R || gy > H - 1 + R) continue;  // no in-frame window reaches it
+    const int src = border_src(gy, H, border) - ys;
+    for (int c = c0 + lane; c <= c1; c += 32) S[row * BW + c] = S[src * BW + c];
   }
   __syncwarp();
-  if (lft > cmin || rgt < cmax) {
+  const int jlo = cmin > -R - xs ? cmin : -R - xs;          // columns with frame x >= -R
+  const int jhi = cmax < W - 1 + R - xs ? cmax : W - 1 + R - xs;
+  if (lft > jlo || rgt < jhi) {
     for (int row = row0 + lane; row < row1; row += 32) {
       T *Rw = S + row * BW;
-      if (lft > cmin) {
-        const T v = Rw[lft];
-        for (int j = cmin; j < lft; ++j) Rw[j] = v;
-      }
-      if (rgt < cmax) {
-        const T v = Rw[rgt];
-        for (int j = rgt + 1; j <= cmax; ++j) Rw[j] = v;
-      }
+      for (int j = jlo; j < lft; ++j) Rw[j] = Rw[border_src(xs + j, W, border) - xs];
+      for (int j = rgt + 1; j <= jhi; ++j) Rw[j] = Rw[border_src(xs + j, W, border) - xs];
     }
   }
   __syncwarp();
@@ -753,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
           tma_load_2d(S, &frame_ptr(p, ti.f)->tin, &full[s], xs, ys);
         }
       } else {
-        plain_tile_load<T>(frame_ptr(p, ti.f), xs, ys, S, BW, BH, lane);
+        plain_tile_load<T>(frame_ptr(p, ti.f), xs, ys, S, BW, BH, p.border, lane);
         fence_proxy_async_smem();  // these generic writes precede a later TMA refill of the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[s]);
@@ -790,8 +803,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
     if (live && ALGO == ALGO_DENSE3) {
-      if (tma_in && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
-        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, lane);
+      if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
+                           p.border, lane);
       // results go straight from registers to the frame (no output tile)
       const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
@@ -812,8 +826,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
                                       lane, flagged);
       }
     } else if (live) {
-      if (tma_in && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
-        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, lane);
+      if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
+                           p.border, lane);
       if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
       __syncwarp();
       int flagged = 0;

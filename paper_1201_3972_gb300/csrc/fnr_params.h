@@ -44,7 +44,12 @@ struct alignas(128) FnrParams {
   unsigned int *status;            // device status word (bit 0: bounded wait timed out)
   unsigned long long *launches;    // device launch counter (nullable)
   int mode;                        // kModeFnr, or kModeMedian: every pixel is treated as noisy
+  int border;                      // kBorderReplicate / kBorderMirror / kBorderZero
 };
+
+constexpr int kBorderReplicate = 0;  // clamp to the nearest edge pixel (default)
+constexpr int kBorderMirror = 1;     // reflect about the edge pixel: d c b | a b c d | c b a
+constexpr int kBorderZero = 2;       // outside pixels read 0
 
 constexpr int kModeFnr = 0;        // replace only pixels equal to a window extreme (Sec. 3.3-3.4)
 constexpr int kModeMedian = 1;     // standard median filter: replace every pixel (the paper's MF, Sec. 2)

@@ -66,6 +66,7 @@ struct ir_filter {
   size_t scratch_bytes = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   ir_kernel_config cfg[2][kNumK];
+  int border = kBorderReplicate;
   std::string last_error;
   std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, smem) -> CTAs per SM
   std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
@@ -310,6 +311,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.prm.status = h->d_status;
   cl.prm.launches = h->d_launches;
   cl.prm.mode = mode;
+  cl.prm.border = h->border;
   ir_status s = host_prepare_class(h, cl);
   if (s != IR_OK) return s;
   if (flagged) IR_CUDA(h, cudaMemsetAsync(flagged, 0, sizeof(unsigned long long), st));
@@ -473,6 +475,18 @@ unsigned long long ir_filter_launch_count(const ir_filter *h) {
   return n;
 }
 
+ir_status ir_filter_set_border(ir_filter *h, ir_border mode) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (mode != IR_BORDER_REPLICATE && mode != IR_BORDER_MIRROR && mode != IR_BORDER_ZERO)
+    return fail(h, IR_EINVAL, "unknown border mode %d", static_cast<int>(mode));
+  h->border = static_cast<int>(mode);
+  return IR_OK;
+}
+
+ir_border ir_filter_get_border(const ir_filter *h) {
+  return h ? static_cast<ir_border>(h->border) : IR_BORDER_REPLICATE;
+}
+
 ir_status ir_filter_get_config(ir_filter *h, ir_dtype dtype, int k, ir_kernel_config *out) {
   if (!h || !out) return fail(h, IR_EINVAL, "null argument");
   if (!valid_dtype(dtype) || !valid_k(k)) return fail(h, IR_EINVAL, "bad dtype or k");
@@ -547,6 +561,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     cl.prm.tile_h = cl.cfg.tile_h;
     cl.prm.status = h->d_status;
     cl.prm.launches = h->d_launches;
+    cl.prm.border = h->border;
     ir_status s = host_prepare_class(h, cl);
     if (s != IR_OK) return s;
     plan->classes.push_back(cl);
@@ -618,9 +633,10 @@ ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, v
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
   PlanKey key;
-  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg));
+  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border));
   std::memcpy(key.bytes.data(), descs, sizeof(ir_frame_desc) * n);
   std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n, h->cfg, sizeof(h->cfg));
+  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n + sizeof(h->cfg), &h->border, sizeof(h->border));
   auto it = h->plans.find(key);
   ir_batch_plan *plan = nullptr;
   if (it != h->plans.end()) {

@@ -85,3 +85,32 @@ def test_table1_ordering_on_synthetic_frames(flt):
         assert r["fnr2_psnr"] > r["fnr1_psnr"], (key, r)
         assert r["mf1_sorts"] == [H * W]
         assert r["fnr1_sorts"][0] < H * W
+
+
+@pytest.mark.parametrize("border", ["mirror", "zero", "replicate"])
+@pytest.mark.parametrize("k", [3, 5, 7, 9, 15, 21])
+def test_border_modes_match_oracle(flt, border, k):
+    """Every strategy, TMA-staged (aligned pitch) and plain-staged (odd pitch)
+    frames, frames smaller than the window."""
+    rng = np.random.default_rng(60 + k)
+    flt.set_border(border)
+    try:
+        for es, dt in ((1, _lib.IR_U8), (2, _lib.IR_U16)):
+            npdt = np.uint8 if es == 1 else np.uint16
+            for algo in _algos(k):
+                flt.set_config(dt, k, 64, 64, algo)
+                for H, W, pitch in ((70, 133, 144), (70, 133, 137), (5, 3, 16), (1, 40, 48), (130, 64, 64)):
+                    a = rng.integers(0, 256 if es == 1 else 65536, (H, W)).astype(npdt)
+                    want, wf = oracle.fnr_border(a, k, border)
+                    ib, ia, ip = upload(a, pitch)
+                    ob, oa, op = empty_like_frame(a, pitch)
+                    import torch
+                    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+                    flt.ir_filter_run2(ia, ip, oa, op, H, W, dt, k, None, ctr)
+                    got = download(ob, oa, op, H, W, npdt)
+                    np.testing.assert_array_equal(got, want, err_msg=f"{border} k{k} algo{algo} {H}x{W} p{pitch}")
+                    assert int(ctr.item()) == wf
+            flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+    finally:
+        flt.set_border("replicate")
+    assert flt.get_border() == _lib.IR_BORDER_REPLICATE

@@ -160,6 +160,25 @@ def test_iterative_passes_are_compositions(oracle_mod):
         assert counts2 == counts
 
 
+@pytest.mark.parametrize("border,mode", [("replicate", "nearest"), ("mirror", "mirror"), ("zero", "constant")])
+def test_border_readings_match_library(oracle_mod, border, mode):
+    """Each border reading equals scipy's filters with the same extension:
+    nearest (replicate), mirror (d c b | a b c d | c b a) and constant 0,
+    including windows wider than the frame."""
+    rng = np.random.default_rng(21)
+    for H, W in ((1, 1), (1, 6), (2, 3), (4, 9), (11, 7), (16, 23)):
+        for k in (3, 5, 7, 9, 21):
+            for style in ("uniform", "few"):
+                a = rand_frame(rng, H, W, synth.U8, style)
+                mn = nd.minimum_filter(a, size=k, mode=mode, cval=0)
+                mx = nd.maximum_filter(a, size=k, mode=mode, cval=0)
+                md = nd.median_filter(a, size=k, mode=mode, cval=0)
+                flag = (a == mn) | (a == mx)
+                got, f = oracle_mod.fnr_border(a, k, border)
+                np.testing.assert_array_equal(got, np.where(flag, md, a).astype(a.dtype), err_msg=f"{H}x{W} k{k}")
+                assert f == int(flag.sum())
+
+
 def test_pitched_input(oracle_mod):
     rng = np.random.default_rng(5)
     a = rng.integers(0, 65536, (11, 13)).astype(np.uint16)
