@@ -117,3 +117,15 @@ def test_full_mixed_batch_256_frames(flt):
     items = _stage(frames)
     flt.ir_filter_run_batch(_descs(items), len(items))
     _verify(items)
+
+
+def test_batch_beyond_the_shared_directory(flt):
+    """More frames in one class than the kernel's shared-memory frame
+    directory holds (512): tiles are then located by a search of the frame
+    table in global memory."""
+    rng = np.random.default_rng(17)
+    frames = [(rng.integers(0, 256, (int(rng.integers(1, 40)), int(rng.integers(1, 70)))).astype(np.uint8), 3, False)
+              for _ in range(600)]
+    items = _stage(frames)
+    flt.ir_filter_run_batch(_descs(items), len(items))
+    _verify(items, threads=4)
