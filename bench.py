@@ -155,9 +155,11 @@ def own_arm(args):
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0")) % max(1, torch.cuda.device_count())
     if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        # frames are independent: nothing on the data path is collective; the
+        # process group only carries the barriers and the max over ranks
+        dist.init_process_group("gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     _build.build()
@@ -213,6 +215,10 @@ def own_arm(args):
     torch.cuda.synchronize()
     total_ms = t_start.elapsed_time(t_end)
     gpu_launches = flt.launch_count() - l0
+    if world > 1:  # launches of the whole job
+        lt = torch.tensor([gpu_launches], dtype=torch.int64)
+        dist.all_reduce(lt, op=dist.ReduceOp.SUM)
+        gpu_launches = int(lt.item())
     if world > 1:
         dist.barrier()
     # per-window classes timed alone (the dominant-kernel roofline comes from these)
@@ -263,7 +269,7 @@ def own_arm(args):
 
     ms_step = total_ms / args.steps
     if world > 1:
-        t = torch.tensor([ms_step], device=dev)
+        t = torch.tensor([ms_step], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     value = world * step_px / (ms_step * 1e-3) / 1e6
@@ -419,7 +425,8 @@ def reference_arm(args):
     px = sum(f.size for f in frames)
     value = px / dt / 1e6
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1,
+        "impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frame": "640x512 uint16 14-bit", "frames_per_step": len(frames)},
