@@ -303,19 +303,50 @@ __device__ __forceinline__ void store_row8<uint8_t>(uint8_t *q, const uint32_t (
   *reinterpret_cast<uint2 *>(q) = make_uint2(__byte_perm(v[0], v[1], 0x6420), __byte_perm(v[2], v[3], 0x6420));
 }
 
-__device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
-  return vmax2(vmin2(a, b), vmin2(vmax2(a, b), c));
+// Integer multiply-add on the FMA pipe: a * b + c (mod 2^32).
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
 }
+
+// Operations of the selection networks on two pixels per 32-bit word.
+// A full compare-exchange needs min and max of the same two words; the
+// packed min/max both run on the integer ALU pipe, which bounds the median
+// stage. For 16-bit halves max = a + b - min holds per half, and the 32-bit
+// sum a + b - min is exact modulo 2^32 (the carries of the low half cancel),
+// so part of the exchanges take their max as two multiply-adds on the
+// otherwise idle FMA pipe (the dense 3x3 path uses the same identity for its
+// medians of three and its lane-wise differences). `unit` is 1 and `neg` is 0xffffffff, read from
+// the launch parameters so that the compiler keeps them as multiplies.
+struct PackedOp {
+  // of every kCxPeriod full exchanges, kCxAlu take the ALU max (measured best
+  // split for the k=5/7 networks on GB300)
+  static constexpr int kCxPeriod = 5, kCxAlu = 2;
+  uint32_t unit, neg;
+  __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) const { return vmin2(a, b); }
+  __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) const { return vmax2(a, b); }
+  // median of three as their sum minus min and max: two (3-input) ALU ops and
+  // four multiply-adds instead of four ALU ops; exact modulo 2^32 as above
+  __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) const {
+    const uint32_t mn = vmin2(vmin2(a, b), c), mx = vmax2(vmax2(a, b), c);
+    return imad(mx, neg, imad(mn, neg, imad(c, unit, imad(a, unit, b))));
+  }
+  // a - b per 16-bit lane, for lanes where a >= b (no borrow between lanes)
+  __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b) const { return imad(b, neg, a); }
+  template <int J>
+  __device__ __forceinline__ void cx(uint32_t &a, uint32_t &b) const {
+    const uint32_t lo = vmin2(a, b);
+    if (J % kCxPeriod < kCxAlu)
+      b = vmax2(a, b);
+    else
+      b = imad(lo, neg, imad(a, unit, b));
+    a = lo;
+  }
+};
 
 // (hi lane of a, lo lane of b): the odd-aligned pair between two even pairs.
 __device__ __forceinline__ uint32_t odd_pair(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5432); }
-
-// Per 16-bit lane: 1 where g_min < c < g_max (signal pixel), 0 where c equals
-// g_min or g_max (noisy). c - g_min and g_max - c never borrow across lanes
-// because every lane satisfies g_min <= c <= g_max.
-__device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint32_t gmax) {
-  return vmin2(vmin2(c - gmin, gmax - c), 0x00010001u);
-}
 
 // Output rows [r0, r0+SR) of the tile, written straight to the frame: 16-byte
 // (u16) or 8-byte (u8) stores when the 8 pixels are inside the frame and the
@@ -324,7 +355,8 @@ __device__ __forceinline__ uint32_t signal_bits(uint32_t c, uint32_t gmin, uint3
 // power of two (seg_shift = log2 of it).
 template <typename T, bool COUNT, bool ALL>
 __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int TW, int BW, int r0, int SR,
-                             int seg_shift, int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged) {
+                             int seg_shift, int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged,
+                             const PackedOp op) {
   constexpr int XOFF = xoff_for(1, sizeof(T));
   const int items = (SR >> 1) << seg_shift;
   const int seg_mask = (1 << seg_shift) - 1;
@@ -363,12 +395,15 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
         const uint32_t mlo = lo[o][pp + 1], mmd = md[o][pp + 1], mhi = hi[o][pp + 1];
         const uint32_t maxlo = vmax2(vmax2(olo[pp], mlo), olo[pp + 1]);
         const uint32_t gmin = vmin2(vmin2(olo[pp], mlo), olo[pp + 1]);
-        const uint32_t medmd = med3v(omd[pp], mmd, omd[pp + 1]);
+        const uint32_t medmd = op.med3(omd[pp], mmd, omd[pp + 1]);
         const uint32_t minhi = vmin2(vmin2(ohi[pp], mhi), ohi[pp + 1]);
         const uint32_t gmax = vmax2(vmax2(ohi[pp], mhi), ohi[pp + 1]);
-        const uint32_t gm = med3v(maxlo, medmd, minhi);
+        const uint32_t gm = op.med3(maxlo, medmd, minhi);
         const uint32_t c = e[1 + o][pp + 1];
-        const uint32_t sig = ALL ? 0u : signal_bits(c, gmin, gmax);  // ALL: standard median filter
+        // per 16-bit lane: 1 where g_min < c < g_max (signal pixel), 0 where c
+        // equals g_min or g_max (noisy); c - g_min and g_max - c never borrow
+        // across lanes since g_min <= c <= g_max. ALL: standard median filter
+        const uint32_t sig = ALL ? 0u : vmin2(vmin2(op.sub(c, gmin), op.sub(gmax, c)), 0x00010001u);
         const uint32_t keep = sig * 0xffffu;
         res[pp] = (c & keep) | (gm & ~keep);
         if constexpr (COUNT) {
@@ -600,16 +635,21 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
   return base;
 }
 
-struct PackedOp {
-  __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) const { return vmin2(a, b); }
-  __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) const { return vmax2(a, b); }
-};
-
 // Flagged pixels of the strip, two per lane: the two k x k windows are
 // gathered into the low and high 16-bit lanes of the same registers and one
 // packed selection network serves both (an odd tail pixel pairs with itself).
+//
+// 16-bit pixels are gathered as 32-bit words: a window row of K = 2R+1
+// pixels always lies in R+1 aligned words, whose 2R+2 halves hold the row
+// plus one unused half, the first (pixel at an odd element) or the last (at
+// an even one). The halves 1..2R are pixels of the row whatever the parity,
+// so they pair up between the two pixels with fixed selectors; the one
+// remaining pixel of each row (half 0 or half 2R+1) is picked with a
+// per-pixel selector. The network does not care in which order a window's
+// values arrive, only that each register holds one value of each pixel.
 template <typename T, int K>
-__device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane) {
+__device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane,
+                              PackedOp op) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
   const int pairs = (F + 1) >> 1;
@@ -617,15 +657,39 @@ __device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int
     const int ea = list[2 * i];
     const int eb = 2 * i + 1 < F ? list[2 * i + 1] : ea;
     const int ya = r0 + (ea >> 8), xa = ea & 255, yb = r0 + (eb >> 8), xb = eb & 255;
-    const T *ba = S + ya * BW + (XOFF - R) + xa;
-    const T *bb = S + yb * BW + (XOFF - R) + xb;
     uint32_t v[K * K];
+    if constexpr (sizeof(T) == 2) {
+      const uint32_t *W32 = reinterpret_cast<const uint32_t *>(S);
+      const int BWW = BW >> 1;  // BW is even: rows start on a word
+      const int sa = ya * BW + (XOFF - R) + xa, sb = yb * BW + (XOFF - R) + xb;
+      const uint32_t *wa = W32 + (sa >> 1), *wb = W32 + (sb >> 1);
+      // leftover pixel: low half of word 0 (even start) or high half of word R (odd start)
+      const uint32_t sel_a = (sa & 1) ? 0x0076u : 0x0010u;
+      const uint32_t sel_b = (sb & 1) ? 0x7600u : 0x1000u;
 #pragma unroll
-    for (int a = 0; a < K; ++a)
+      for (int a = 0; a < K; ++a) {
+        uint32_t ua[R + 1], ub[R + 1];
 #pragma unroll
-      for (int b = 0; b < K; ++b)
-        v[a * K + b] = __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
-    const uint32_t m = MedianNet<K>::run(v, PackedOp{});
+        for (int t = 0; t <= R; ++t) {
+          ua[t] = wa[a * BWW + t];
+          ub[t] = wb[a * BWW + t];
+        }
+#pragma unroll
+        for (int h = 1; h <= 2 * R; ++h)
+          v[a * K + h - 1] = __byte_perm(ua[h >> 1], ub[h >> 1], (h & 1) ? 0x7632u : 0x5410u);
+        v[a * K + 2 * R] = __byte_perm(__byte_perm(ua[0], ua[R], sel_a), __byte_perm(ub[0], ub[R], sel_b), 0x7610u);
+      }
+    } else {
+      const T *ba = S + ya * BW + (XOFF - R) + xa;
+      const T *bb = S + yb * BW + (XOFF - R) + xb;
+#pragma unroll
+      for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int b = 0; b < K; ++b)
+          v[a * K + b] =
+              __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
+    }
+    const uint32_t m = MedianNet<K>::run(v, op);
     O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
     O[yb * TW + xb] = static_cast<T>(m >> 16);
   }
@@ -803,6 +867,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
     if (live && ALGO == ALGO_DENSE3) {
+      const PackedOp d3op{p.unit, 0u - p.unit};
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
         fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
                            p.border, lane);
@@ -811,19 +876,19 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       int flagged = 0;
       if (p.mode == kModeMedian) {
         dense3_strip<T, false, true>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                                     flagged);
+                                     flagged, d3op);
         if (cur.counted && lane == 0) {  // every in-frame pixel of the strip takes a median
           const int rows = min(SR, cur.H - y0 - r0), cols = min(TW, cur.W - x0);
           atomicAdd(cf->flagged, static_cast<unsigned long long>(rows) * static_cast<unsigned long long>(cols));
         }
       } else if (cur.counted) {
         dense3_strip<T, true, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                                     flagged);
+                                     flagged, d3op);
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if (lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else {
         dense3_strip<T, false, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
-                                      lane, flagged);
+                                      lane, flagged, d3op);
       }
     } else if (live) {
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
@@ -841,7 +906,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.np, r0, SR, cur.W - x0, cur.H - y0,
                                          p.mode == kModeMedian, divG, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
-          network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
+          network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane, PackedOp{p.unit, 0u - p.unit});
         } else {
           uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
           const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, L.nbmax, lane);

@@ -45,6 +45,7 @@ struct alignas(128) FnrParams {
   unsigned long long *launches;    // device launch counter (nullable)
   int mode;                        // kModeFnr, or kModeMedian: every pixel is treated as noisy
   int border;                      // kBorderReplicate / kBorderMirror / kBorderZero
+  unsigned int unit = 1u;          // always 1: multiplier of the median networks' multiply-add form
 };
 
 constexpr int kBorderReplicate = 0;  // clamp to the nearest edge pixel (default)

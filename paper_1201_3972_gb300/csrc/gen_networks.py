@@ -17,6 +17,11 @@ Construction:
 Pruning walks the network backwards keeping only compare-exchanges whose
 min or max output is still live; a half that is never read is not emitted.
 
+A compare-exchange whose two outputs are both live is emitted as
+``op.cx<j>(a, b)`` with j its index among such exchanges, so that the
+operation type can spread them over different execution units; one with a
+single live output is a lone ``op.mn`` or ``op.mx``.
+
 Run this file to rewrite ``fnr_networks.cuh``; the tests import it to check
 each network with the 0-1 principle and that the header is up to date.
 """
@@ -113,9 +118,11 @@ def emit() -> str:
         lines.append(f"template <> struct MedianNet<{k}> {{")
         lines.append(f"  static constexpr int kOps = {op_count(net)};")
         lines.append(f"  template <class Op> __device__ __forceinline__ static uint32_t run(uint32_t (&v)[{n}], Op op) {{")
+        j = 0
         for a, b, ka, kb in net:
             if ka and kb:
-                lines.append(f"    {{ uint32_t t = op.mn(v[{a}], v[{b}]); v[{b}] = op.mx(v[{a}], v[{b}]); v[{a}] = t; }}")
+                lines.append(f"    op.template cx<{j}>(v[{a}], v[{b}]);")
+                j += 1
             elif ka:
                 lines.append(f"    v[{a}] = op.mn(v[{a}], v[{b}]);")
             else:

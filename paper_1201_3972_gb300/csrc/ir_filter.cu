@@ -301,7 +301,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.esize = esize_of(dtype);
   cl.k = k;
   cl.cfg = h->cfg[cl.esize - 1][kslot(k)];
-  std::memset(&cl.prm, 0, sizeof cl.prm);
+  cl.prm = FnrParams{};
   host_make_frame_dev(h, cl.prm.single, in, in_pitch, out, out_pitch, H, W, cl.esize, k, cl.cfg, flagged);
   cl.prm.table = nullptr;
   cl.prm.nframes = 1;
@@ -554,7 +554,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
       tiles += host[slot].tiles_x * host[slot].tiles_y;
       ++slot;
     }
-    std::memset(&cl.prm, 0, sizeof cl.prm);
+    cl.prm = FnrParams{};
     cl.prm.nframes = static_cast<int>(kv.second.size());
     cl.prm.total_tiles = tiles;
     cl.prm.tile_w = cl.cfg.tile_w;

@@ -171,8 +171,7 @@ extern "C" ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pit
   if (!fn) return err(IR_EUNSUPPORTED, "no kernel built for this window");
   const Layout L = make_layout(esize, k, algo, th, tw);
 
-  FnrParams prm;
-  std::memset(&prm, 0, sizeof prm);
+  FnrParams prm{};
   FrameDev &f = prm.single;
   f.in = st.scratch;
   f.out = static_cast<unsigned char *>(frame);

@@ -418,7 +418,7 @@ ir_status ir_server_open_stream(ir_server *s, int H, int W, ir_dtype dtype, int 
     cl.esize = esize;
     cl.k = k;
     cl.cfg = cfg;
-    std::memset(&cl.prm, 0, sizeof cl.prm);
+    cl.prm = FnrParams{};
     cl.prm.tile_w = cfg.tile_w;
     cl.prm.tile_h = cfg.tile_h;
     cl.prm.status = host_status_word(s->h);

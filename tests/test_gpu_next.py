@@ -114,3 +114,29 @@ def test_border_modes_match_oracle(flt, border, k):
     finally:
         flt.set_border("replicate")
     assert flt.get_border() == _lib.IR_BORDER_REPLICATE
+
+
+@pytest.mark.parametrize("parts", [2, 3, 5])
+def test_row_bands_on_device(flt, parts):
+    """A frame split into row bands: each halo-extended band is filtered as a
+    frame of its own (a sub-frame view of the same device buffer, as a rank
+    holding only those rows would), and the band rows stitched together equal
+    the whole-frame result and the oracle."""
+    from paper_1201_3972_gb300 import shard
+    cases = [(synth.make_frame(517, 300, synth.U14, 31, 8.0, 0.2), 7, _lib.IR_U14),
+             (synth.make_frame(333, 256, synth.U8, 32, 2.0, 0.1), 3, _lib.IR_U8),
+             (synth.make_frame(260, 190, synth.U14, 33, 8.0, 0.2, impulse="rv"), 13, _lib.IR_U14)]
+    for f, k, dt in cases:
+        H, W = f.shape
+        ib, ia, ip = upload(f)
+        want, _ = oracle.fnr_mt(f, k, 16)
+        out = np.empty_like(f)
+        for b in shard.row_bands(H, k, parts):
+            if b.y1 == b.y0:
+                continue
+            sub = f[b.h0:b.h1]
+            ob, oa, op = empty_like_frame(sub)
+            flt.ir_filter_run2(ia + b.h0 * ip, ip, oa, op, b.h1 - b.h0, W, dt, k, None, None)
+            rows = download(ob, oa, op, b.h1 - b.h0, W, f.dtype)
+            out[b.y0:b.y1] = rows[b.y0 - b.h0:b.y1 - b.h0]
+        np.testing.assert_array_equal(out, want)
