@@ -316,8 +316,8 @@ __device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
 // stage. For 16-bit halves max = a + b - min holds per half, and the 32-bit
 // sum a + b - min is exact modulo 2^32 (the carries of the low half cancel),
 // so part of the exchanges take their max as two multiply-adds on the
-// otherwise idle FMA pipe (the dense 3x3 path uses the same identity for its
-// medians of three and its lane-wise differences). `unit` is 1 and `neg` is 0xffffffff, read from
+// otherwise idle FMA pipe (the flag tests take their lane-wise differences
+// there too). `unit` is 1 and `neg` is 0xffffffff, read from
 // the launch parameters so that the compiler keeps them as multiplies.
 struct PackedOp {
   // of every kCxPeriod full exchanges, kCxAlu take the ALU max (measured best
@@ -326,12 +326,6 @@ struct PackedOp {
   uint32_t unit, neg;
   __device__ __forceinline__ uint32_t mn(uint32_t a, uint32_t b) const { return vmin2(a, b); }
   __device__ __forceinline__ uint32_t mx(uint32_t a, uint32_t b) const { return vmax2(a, b); }
-  // median of three as their sum minus min and max: two (3-input) ALU ops and
-  // four multiply-adds instead of four ALU ops; exact modulo 2^32 as above
-  __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) const {
-    const uint32_t mn = vmin2(vmin2(a, b), c), mx = vmax2(vmax2(a, b), c);
-    return imad(mx, neg, imad(mn, neg, imad(c, unit, imad(a, unit, b))));
-  }
   // a - b per 16-bit lane, for lanes where a >= b (no borrow between lanes)
   __device__ __forceinline__ uint32_t sub(uint32_t a, uint32_t b) const { return imad(b, neg, a); }
   template <int J>
@@ -344,6 +338,10 @@ struct PackedOp {
     a = lo;
   }
 };
+
+__device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
+  return vmax2(vmin2(a, b), vmin2(vmax2(a, b), c));
+}
 
 // (hi lane of a, lo lane of b): the odd-aligned pair between two even pairs.
 __device__ __forceinline__ uint32_t odd_pair(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5432); }
@@ -395,10 +393,10 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
         const uint32_t mlo = lo[o][pp + 1], mmd = md[o][pp + 1], mhi = hi[o][pp + 1];
         const uint32_t maxlo = vmax2(vmax2(olo[pp], mlo), olo[pp + 1]);
         const uint32_t gmin = vmin2(vmin2(olo[pp], mlo), olo[pp + 1]);
-        const uint32_t medmd = op.med3(omd[pp], mmd, omd[pp + 1]);
+        const uint32_t medmd = med3v(omd[pp], mmd, omd[pp + 1]);
         const uint32_t minhi = vmin2(vmin2(ohi[pp], mhi), ohi[pp + 1]);
         const uint32_t gmax = vmax2(vmax2(ohi[pp], mhi), ohi[pp + 1]);
-        const uint32_t gm = op.med3(maxlo, medmd, minhi);
+        const uint32_t gm = med3v(maxlo, medmd, minhi);
         const uint32_t c = e[1 + o][pp + 1];
         // per 16-bit lane: 1 where g_min < c < g_max (signal pixel), 0 where c
         // equals g_min or g_max (noisy); c - g_min and g_max - c never borrow
@@ -484,19 +482,6 @@ __device__ __forceinline__ uint32_t pair_word<uint8_t>(const uint8_t *S, int row
   return __byte_perm(static_cast<uint32_t>(*reinterpret_cast<const uint16_t *>(S + row * BW + col)), 0, 0x4140);
 }
 
-template <typename T>
-__device__ __forceinline__ void store_pair(T *O, int idx, uint32_t w);
-
-template <>
-__device__ __forceinline__ void store_pair<uint16_t>(uint16_t *O, int idx, uint32_t w) {
-  *reinterpret_cast<uint32_t *>(O + idx) = w;
-}
-
-template <>
-__device__ __forceinline__ void store_pair<uint8_t>(uint8_t *O, int idx, uint32_t w) {
-  *reinterpret_cast<uint16_t *>(O + idx) = static_cast<uint16_t>(__byte_perm(w, 0, 0x0020));
-}
-
 // Sliding packed extreme (min.u16x2 / max.u16x2) over windows [q, q+K-1] of
 // RG+K-1 words, sharing the core [RG-1, K-1] common to all windows (RG <= K).
 template <int K, int RG, bool MAX>
@@ -523,12 +508,12 @@ __device__ __forceinline__ void sliding_extreme2(const uint32_t (&v)[RG + K - 1]
   }
 }
 
-// Vertical pass over the strip on column pairs: vminP/vmaxP[q][p] = packed
-// min/max of stage columns (cb + 2p, cb + 2p + 1) over stage rows
+// Vertical pass over the strip on column pairs: vminP/vmaxP[q * NPS + p] =
+// packed min/max of stage columns (cb + 2p, cb + 2p + 1) over stage rows
 // r0+q .. r0+q+K-1, q < SR, p < NP.
 template <typename T, int K>
-__device__ void vertical_pairs(const T *S, uint32_t *vminP, uint32_t *vmaxP, int BW, int NP, int cb, int r0, int SR,
-                               const FastDiv &divNP, int lane) {
+__device__ void vertical_pairs(const T *S, uint32_t *vminP, uint32_t *vmaxP, int BW, int NP, int NPS, int cb, int r0,
+                               int SR, const FastDiv &divNP, int lane) {
   constexpr int RG = row_group(K);
   const int items = NP * (SR / RG);
   for (int it = lane; it < items; it += 32) {
@@ -542,59 +527,97 @@ __device__ void vertical_pairs(const T *S, uint32_t *vminP, uint32_t *vmaxP, int
     sliding_extreme2<K, RG, true>(v, mx);
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
-      vminP[(g * RG + q) * NP + p] = mn[q];
-      vmaxP[(g * RG + q) * NP + p] = mx[q];
+      vminP[(g * RG + q) * NPS + p] = mn[q];
+      vmaxP[(g * RG + q) * NPS + p] = mx[q];
     }
   }
 }
 
-// Horizontal pass + flag over the strip, PPI output pairs (2*PPI pixels) per
+// Horizontal pass + flag over the strip, PPI = 4 output pairs (8 pixels) per
 // lane item: every centre value goes to the output tile; flagged in-frame
 // pixels (all in-frame pixels when `all`) are appended to the warp's list as
 // (row in strip << 8 | column). The window of output column x spans stage
 // columns XOFF+x-R .. XOFF+x+R; for a pair (x, x+1) the packed window term at
 // offset d is the pair word at stage column XOFF+x+d, which is a byte permute
 // of two stored words when that column is odd relative to cb (compile time).
-// Returns the list length (warp-uniform).
+// The item's extreme words, centre pixels and output pixels are each moved
+// as 16-byte (8-byte for u8 pixels) vectors. Returns the list length
+// (warp-uniform).
+template <typename T>
+__device__ __forceinline__ void load_centre8(const T *p, uint32_t (&c)[4]);
+
+template <>
+__device__ __forceinline__ void load_centre8<uint16_t>(const uint16_t *p, uint32_t (&c)[4]) {
+  const uint4 v = *reinterpret_cast<const uint4 *>(p);
+  c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+}
+
+template <>
+__device__ __forceinline__ void load_centre8<uint8_t>(const uint8_t *p, uint32_t (&c)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2 *>(p);
+  c[0] = __byte_perm(v.x, 0, 0x4140);
+  c[1] = __byte_perm(v.x, 0, 0x4342);
+  c[2] = __byte_perm(v.y, 0, 0x4140);
+  c[3] = __byte_perm(v.y, 0, 0x4342);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_centre8(T *p, const uint32_t (&c)[4]);
+
+template <>
+__device__ __forceinline__ void store_centre8<uint16_t>(uint16_t *p, const uint32_t (&c)[4]) {
+  *reinterpret_cast<uint4 *>(p) = make_uint4(c[0], c[1], c[2], c[3]);
+}
+
+template <>
+__device__ __forceinline__ void store_centre8<uint8_t>(uint8_t *p, const uint32_t (&c)[4]) {
+  *reinterpret_cast<uint2 *>(p) = make_uint2(__byte_perm(c[0], c[1], 0x6420), __byte_perm(c[2], c[3], 0x6420));
+}
+
 template <typename T, int K>
 __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_t *vmaxP, T *O, uint16_t *list, int TW,
-                                int BW, int NP, int r0, int SR, int tw_valid, int th_valid, bool all,
-                                const FastDiv &divG, int lane) {
+                                int BW, int NPS, int r0, int SR, int tw_valid, int th_valid, bool all,
+                                const FastDiv &divG, const PackedOp op, int lane) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
   constexpr int CB = (XOFF - R) & ~1;
-  constexpr int OFF0 = XOFF - CB;          // stage column XOFF relative to CB
+  constexpr int OFF0 = XOFF - CB;          // stage column XOFF relative to CB (R or R + 1)
   constexpr int PPI = 4;                   // output pairs per item
-  constexpr int W0 = (OFF0 - R) >> 1;      // first word an item reads, relative to 2*pair index / 2
-  constexpr int NW = ((OFF0 + 2 * PPI - 1 + R) >> 1) - W0 + 1;
+  constexpr int NW = ((OFF0 + 2 * PPI - 1 + R) >> 1) + 1;  // words an item reads, from word x0p / 2
+  constexpr int NV = (NW + 3) / 4;         // 16-byte vectors covering them
+  static_assert(OFF0 - R == 0 || OFF0 - R == 1, "first word of an item is x0p / 2");
   const int gpr = TW / (2 * PPI);          // items per row
   const int items = SR * gpr;
   int base = 0;
   for (int it0 = 0; it0 < items; it0 += 32) {
     const int it = it0 + lane;
-    uint32_t fm = 0;
+    uint32_t fm = 0;                       // bit j: pixel 2j flagged; bit 4 + j: pixel 2j + 1
     int q = 0, x0p = 0;
     if (it < items) {
       q = static_cast<int>(divG.div(static_cast<uint32_t>(it)));
       const int grp = it - q * gpr;
       x0p = grp * 2 * PPI;                 // first output column of the item (tile coordinates)
-      const int wbase = (x0p >> 1) + W0;   // = (OFF0 + x0p - R) >> 1 since x0p is even
-      uint32_t mnw[NW], mxw[NW];
+      uint32_t mnw[4 * NV], mxw[4 * NV];
+      const uint4 *vn = reinterpret_cast<const uint4 *>(vminP + q * NPS + (x0p >> 1));
+      const uint4 *vx = reinterpret_cast<const uint4 *>(vmaxP + q * NPS + (x0p >> 1));
 #pragma unroll
-      for (int i = 0; i < NW; ++i) {
-        mnw[i] = vminP[q * NP + wbase + i];
-        mxw[i] = vmaxP[q * NP + wbase + i];
+      for (int i = 0; i < NV; ++i) {
+        const uint4 a = vn[i], b = vx[i];
+        mnw[4 * i] = a.x; mnw[4 * i + 1] = a.y; mnw[4 * i + 2] = a.z; mnw[4 * i + 3] = a.w;
+        mxw[4 * i] = b.x; mxw[4 * i + 1] = b.y; mxw[4 * i + 2] = b.z; mxw[4 * i + 3] = b.w;
       }
       const int ty = r0 + q;
+      uint32_t c[PPI];
+      load_centre8<T>(S + (ty + R) * BW + XOFF + x0p, c);
+      store_centre8<T>(O + ty * TW + x0p, c);
+      uint32_t sig = 0;                    // per 16-bit lane, bit j: pair j is a signal pixel
 #pragma unroll
       for (int j = 0; j < PPI; ++j) {
         uint32_t gmin = 0xffffffffu, gmax = 0u;
 #pragma unroll
         for (int d = -R; d <= R; ++d) {
-          constexpr int dummy = 0;
-          (void)dummy;
           const int col = OFF0 + 2 * j + d;  // relative to x0p, plus OFF0 (compile time)
-          const int w = (col >> 1) - W0;
+          const int w = col >> 1;
           uint32_t a, b;
           if (col & 1) {
             a = __byte_perm(mnw[w], mnw[w + 1], 0x5432);
@@ -606,15 +629,16 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
           gmin = d == -R ? a : vmin2(gmin, a);
           gmax = d == -R ? b : vmax2(gmax, b);
         }
-        const int x = x0p + 2 * j;
-        const uint32_t c = pair_word<T>(S, ty + R, BW, XOFF + x);
-        store_pair<T>(O, ty * TW + x, c);
-        const uint32_t z = vmin2(c - gmin, gmax - c);  // a zero lane: c equals an extreme
-        const bool in_row = ty < th_valid;
-        const bool f0 = in_row && x < tw_valid && (all || (z & 0xffffu) == 0);
-        const bool f1 = in_row && x + 1 < tw_valid && (all || (z >> 16) == 0);
-        fm |= (static_cast<uint32_t>(f0) | (static_cast<uint32_t>(f1) << 1)) << (2 * j);
+        // 1 per 16-bit lane where g_min < c < g_max, 0 where c is an extreme
+        // (no borrow between lanes: g_min <= c <= g_max lane-wise)
+        const uint32_t z = vmin2(vmin2(op.sub(c[j], gmin), op.sub(gmax, c[j])), 0x00010001u);
+        sig = imad(z, op.unit << j, sig);
       }
+      // in-frame pixels of the item, in the bit order of fm
+      const int n = ty < th_valid ? min(max(tw_valid - x0p, 0), 2 * PPI) : 0;
+      const uint32_t valid = ((1u << ((n + 1) >> 1)) - 1u) | (((1u << (n >> 1)) - 1u) << 4);
+      const uint32_t noisy = ~sig & 0x000f000fu;
+      fm = (all ? 0xffu : ((noisy & 0xfu) | (noisy >> 12))) & valid;
     }
     const int cnt = __popc(fm);
     int incl = cnt;
@@ -627,7 +651,7 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
     while (fm) {
       const int bit = __ffs(fm) - 1;
       fm &= fm - 1;
-      list[pos++] = static_cast<uint16_t>((q << 8) | (x0p + bit));
+      list[pos++] = static_cast<uint16_t>((q << 8) | (x0p + ((bit & 3) << 1) + (bit >> 2)));
     }
     base += __shfl_sync(0xffffffffu, incl, 31);
   }
@@ -901,10 +925,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
         uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
         uint32_t *vmax = reinterpret_cast<uint32_t *>(wbase + L.w_vmax);
-        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.cb, r0, SR, divNP, lane);
+        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
         __syncwarp();
-        flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.np, r0, SR, cur.W - x0, cur.H - y0,
-                                         p.mode == kModeMedian, divG, lane);
+        flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
+                                         p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane, PackedOp{p.unit, 0u - p.unit});
         } else {

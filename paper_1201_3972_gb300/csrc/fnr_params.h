@@ -85,6 +85,7 @@ __host__ __device__ constexpr int tile_h_multiple(int k, int algo) {
 struct Layout {
   int r, bw, bh, vw, pw, nbmax, sr;
   int cb, np;          // packed column pairs: first stage column (even) and words per row
+  int nps;             // row stride of the per-warp extreme words (np padded for 16-byte reads)
   int off_stage[kMaxStages];
   int off_out[2];
   int off_warp;        // first per-warp block
@@ -107,6 +108,15 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   // pair words cover stage columns [cb, cb + 2 np): every column a window reads
   L.cb = (xoff - L.r) & ~1;
   L.np = (xoff + tile_w + L.r - 1 - L.cb) / 2 + 1;
+  {
+    // the horizontal pass reads the words of 8 output columns as 16-byte
+    // vectors: nw words from word x0/2, rounded up to whole vectors
+    const int par = (xoff - L.r) & 1;
+    const int nw = ((2 * L.r + par + 7) >> 1) + 1;
+    const int nwr = (nw + 3) & ~3;
+    const int need = tile_w / 2 - 4 + nwr;
+    L.nps = align_up(L.np > need ? L.np : need, 4);
+  }
   L.pw = (L.bw + 31) / 32 + 1;
   L.nbmax = 8 * esize;
   L.sr = tile_h / kConsumerWarps;
@@ -126,8 +136,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   int w = 0;
   if (algo != ALGO_DENSE3) {
     L.w_list = w; w += align_up(L.sr * tile_w * 2, 16);
-    L.w_vmin = w; w += align_up(L.sr * L.np * 4, 16);
-    L.w_vmax = w; w += align_up(L.sr * L.np * 4, 16);
+    L.w_vmin = w; w += align_up(L.sr * L.nps * 4, 16);
+    L.w_vmax = w; w += align_up(L.sr * L.nps * 4, 16);
   }
   if (algo == ALGO_BITPLANE) {
     L.w_planes = w; w += align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);

@@ -121,6 +121,46 @@ def test_median_network_random(k):
         assert gn.apply(net, v)[out] == sorted(v)[(n - 1) // 2]
 
 
+@pytest.mark.parametrize("k", [7, 9])
+def test_median_network_zero_one_near_median(k):
+    """0-1 inputs whose count of ones is within 3 of the median boundary, where
+    a wrong selection network fails first (random positions, 20000 each)."""
+    net, out = gn.median_network(k)
+    n = k * k
+    m = (n - 1) // 2
+    rng = np.random.default_rng(100 + k)
+    for ones in range(n - m - 3, n - m + 4):
+        X = np.zeros((20000, n), dtype=bool)
+        for row in X:
+            row[rng.choice(n, ones, replace=False)] = True
+        wires = [X[:, i].copy() for i in range(n)]
+        for a, b, _, _ in net:
+            wires[a], wires[b] = wires[a] & wires[b], wires[a] | wires[b]
+        assert np.all(wires[out] == ((n - ones) <= m))
+
+
+def test_pairwise_network_sorts():
+    """Parberry's pairwise network sorts: every 0-1 input on 16 wires, and
+    random inputs on the padded 49- and 81-wire forms (all wires checked)."""
+    N = 16
+    idx = np.arange(1 << N, dtype=np.uint32)
+    wires = [((idx >> i) & 1).astype(bool) for i in range(N)]
+    for a, b in gn.pairwise(N):
+        wires[a], wires[b] = wires[a] & wires[b], wires[a] | wires[b]
+    ones = np.bitwise_count(idx).astype(np.int64)
+    for i in range(N):
+        assert np.array_equal(wires[i], i >= N - ones)
+    rng = np.random.default_rng(7)
+    for n in (25, 49, 81):
+        ces = gn.pairwise_padded(n)
+        for _ in range(300):
+            v = rng.integers(0, 1000, n).tolist()
+            for a, b in ces:
+                if v[a] > v[b]:
+                    v[a], v[b] = v[b], v[a]
+            assert v == sorted(v)
+
+
 def test_generated_header_is_current():
     with open(gn.HEADER) as fh:
         assert fh.read() == gn.emit()
