@@ -26,7 +26,11 @@ void host_make_frame_dev(ir_filter *h, FrameDev &f, const void *in, size_t in_pi
 // Resolve the kernel, set its shared-memory attribute, size the persistent grid
 // (cl.prm.total_tiles must be set).
 ir_status host_prepare_class(ir_filter *h, ClassLaunch &cl);
+// Launch on st; a launch without a tile-order slot takes the handle's next one.
 ir_status host_launch_class(ir_filter *h, ClassLaunch &cl, cudaStream_t st);
+// Tile-order slots of the handle for launches outside a batch plan.
+constexpr unsigned kSchedSlots = 256;
+unsigned *host_sched_slot(ir_filter *h);
 ir_kernel_config host_config(const ir_filter *h, int esize, int k);
 int host_device(const ir_filter *h);
 int host_sm_count(const ir_filter *h);

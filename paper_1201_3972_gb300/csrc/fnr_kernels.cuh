@@ -425,6 +425,10 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
   }
 }
 
+#ifndef FNR_SPARSE_LIMIT
+#define FNR_SPARSE_LIMIT 16
+#endif
+
 // ---------------------------------------------------------------------------
 // Compacted strategies (any k): separable g_min/g_max over the warp's strip,
 // flag, warp-local list of flagged pixels, then one median per flagged pixel.
@@ -784,6 +788,83 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
   }
 }
 
+// Sparse strips (few flagged pixels): building the strip's bit planes costs
+// the same however few pixels need a median, so below a threshold the whole
+// warp selects the medians of two flagged pixels at a time instead, packed in
+// the two 16-bit halves of each register. Lane l holds the window cells
+// l, l + 32, ... (n = K*K of them) of both pixels; a median is fixed MSB
+// first: with the bits above b already those of the answer, the cells whose
+// bits from b up equal that prefix followed by a 0 are counted over the warp
+// (one reduction per bit for both pixels); the answer takes a 0 bit when the
+// remaining rank falls among them, else a 1 bit and the rank drops by their
+// count.
+template <typename T, int K>
+__device__ void radix_sparse_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane) {
+  constexpr int R = (K - 1) / 2;
+  constexpr int N = K * K;
+  constexpr int NV = (N + 31) / 32;
+  constexpr int XOFF = xoff_for(R, sizeof(T));
+  int off[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int i = lane + 32 * j;
+    off[j] = i < N ? (i / K) * BW + (i % K) : 0;
+  }
+  const bool last_valid = lane + 32 * (NV - 1) < N;  // the other slots are always window cells
+  for (int e = 0; e < F; e += 2) {
+    const int ea = list[e];
+    const int eb = e + 1 < F ? list[e + 1] : ea;
+    const T *ba = S + (r0 + (ea >> 8)) * BW + (XOFF - R) + (ea & 255);
+    const T *bb = S + (r0 + (eb >> 8)) * BW + (XOFF - R) + (eb & 255);
+    uint32_t w[NV];
+    uint32_t orv = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      w[j] = static_cast<uint32_t>(ba[off[j]]) | (static_cast<uint32_t>(bb[off[j]]) << 16);
+      if (j < NV - 1 || last_valid) orv |= w[j];
+    }
+    orv = __reduce_or_sync(0xffffffffu, orv);
+    const int nb = 32 - __clz(static_cast<int>((orv | (orv >> 16)) & 0xffffu));
+    uint32_t rank_a = (N - 1) / 2, rank_b = (N - 1) / 2, res = 0;  // res: answer of a (low) and b (high)
+    for (int bit = nb - 1; bit >= 0; --bit) {
+      const uint32_t keep = (0xffffu >> bit) * 0x00010001u;  // the bits from `bit` up, per half
+      const uint32_t want = (res >> bit) & keep;             // both answers' prefixes, then a 0
+      uint32_t t[NV];  // per half: 1 where the cell does not match
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        t[j] = vmin2(((w[j] >> bit) & keep) ^ want, 0x00010001u);
+        if (j == NV - 1 && !last_valid) t[j] = 0x00010001u;
+      }
+      // balanced sum: the bit loop is a serial chain, keep its depth short
+#pragma unroll
+      for (int st = 1; st < NV; st <<= 1)
+#pragma unroll
+        for (int j = 0; j + st < NV; j += 2 * st) t[j] += t[j + st];
+      const uint32_t miss = t[0];
+      // matches of both pixels in one reduction (each count <= 441 fits a half)
+      const uint32_t c = static_cast<uint32_t>(NV * 32) * 0x00010001u - __reduce_add_sync(0xffffffffu, miss);
+      const uint32_t ca = c & 0xffffu, cb = c >> 16;
+      if (rank_a >= ca) {  // warp-uniform
+        rank_a -= ca;
+        res |= 1u << bit;
+      }
+      if (rank_b >= cb) {
+        rank_b -= cb;
+        res |= 0x10000u << bit;
+      }
+    }
+    if (lane == 0) O[(r0 + (ea >> 8)) * TW + (ea & 255)] = static_cast<T>(res & 0xffffu);
+    if (lane == 1 && e + 1 < F) O[(r0 + (eb >> 8)) * TW + (eb & 255)] = static_cast<T>(res >> 16);
+  }
+}
+
+// Flagged pixels per strip up to which the bit-plane strategy selects per
+// pixel across the warp (radix_sparse_strip) rather than building planes.
+template <int K>
+struct SparseLimit {
+  static constexpr int value = FNR_SPARSE_LIMIT;
+};
+
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
@@ -830,6 +911,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------- producer
+    // Tiles are handed out by an atomic counter when the launch has one (tiles
+    // differ in cost: a strip's median work grows with its flagged pixels),
+    // else in static round robin.
     for (int i = 0;; ++i) {
       const int s = i % NS, use = i / NS;
       // the stage's previous tile (i - NS) must be released by every consumer warp
@@ -837,7 +921,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         if (lane == 0) atomicOr(p.status, kStatusTimeout);
         break;
       }
-      const TileInfo ti = locate_tile(p, dir, blockIdx.x + i * static_cast<int>(gridDim.x));
+      int tile = blockIdx.x + i * static_cast<int>(gridDim.x);
+      if (p.sched != nullptr) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&p.sched[0], 1u);
+        tile = static_cast<int>(min(__shfl_sync(0xffffffffu, t, 0), 0x7fffffffu));
+      }
+      const TileInfo ti = locate_tile(p, dir, tile);
       T *const S = stage_ptr(s);
       if (lane == 0) info[s] = ti;
       if (!ti.valid) {
@@ -858,6 +948,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         fence_proxy_async_smem();  // these generic writes precede a later TMA refill of the stage
         __syncwarp();
         if (lane == 0) mbar_arrive(&full[s]);
+      }
+    }
+    if (p.sched != nullptr && lane == 0) {
+      // this CTA takes no more tiles; the last CTA to get here resets the slot
+      __threadfence();
+      if (atomicAdd(&p.sched[1], 1u) == gridDim.x - 1) {
+        __threadfence();
+        p.sched[0] = 0u;
+        p.sched[1] = 0u;
       }
     }
     return;
@@ -931,6 +1030,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
                                          p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane, PackedOp{p.unit, 0u - p.unit});
+        } else if (flagged <= SparseLimit<K>::value) {
+          radix_sparse_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {
           uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
           const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, L.nbmax, lane);

@@ -43,6 +43,10 @@ struct alignas(128) FnrParams {
   int tile_w, tile_h;
   unsigned int *status;            // device status word (bit 0: bounded wait timed out)
   unsigned long long *launches;    // device launch counter (nullable)
+  // dynamic tile order (nullable: static round robin): sched[0] hands out tile
+  // indices, sched[1] counts CTAs that are done; the last CTA zeroes both, so
+  // a slot is ready for the next launch ordered after this one
+  unsigned int *sched;
   int mode;                        // kModeFnr, or kModeMedian: every pixel is treated as noisy
   int border;                      // kBorderReplicate / kBorderMirror / kBorderZero
   unsigned int unit = 1u;          // always 1: multiplier of the median networks' multiply-add form

@@ -8,6 +8,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -62,6 +63,8 @@ struct ir_filter {
   int max_smem = 0;
   unsigned *d_status = nullptr;
   unsigned long long *d_launches = nullptr;
+  unsigned *d_sched = nullptr;  // kSchedSlots tile-order slots (2 words each) for one-off launches
+  std::atomic<unsigned> sched_next{0};  // also taken by a server's batcher thread
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -77,6 +80,7 @@ struct ir_filter {
 struct ir_batch_plan {
   ir_filter *h = nullptr;
   FrameDev *d_table = nullptr;
+  unsigned *d_sched = nullptr;  // one tile-order slot per class kernel
   std::vector<ClassLaunch> classes;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -247,6 +251,12 @@ int fnr::host_sm_count(const ir_filter *h) { return h->sm_count; }
 unsigned *fnr::host_status_word(const ir_filter *h) { return h->d_status; }
 unsigned long long *fnr::host_launch_counter(const ir_filter *h) { return h->d_launches; }
 
+// Launches that are not part of a plan take the handle's slots in turn: each
+// kernel resets its slot when it ends, and a slot is only reused kSchedSlots
+// launches later, so launches in flight together on several streams get
+// different slots unless more than kSchedSlots of them overlap.
+unsigned *fnr::host_sched_slot(ir_filter *h) { return h->d_sched + 2 * (h->sched_next.fetch_add(1) % kSchedSlots); }
+
 ir_status fnr::host_prepare_class(ir_filter *h, ClassLaunch &cl) {
   cl.fn = get_kernel(cl.esize, cl.k, cl.cfg.algo);
   if (!cl.fn) return fail(h, IR_EUNSUPPORTED, "no kernel built for esize=%d k=%d algo=%d", cl.esize, cl.k, cl.cfg.algo);
@@ -273,6 +283,7 @@ ir_status fnr::host_prepare_class(ir_filter *h, ClassLaunch &cl) {
 }
 
 ir_status fnr::host_launch_class(ir_filter *h, ClassLaunch &cl, cudaStream_t st) {
+  if (cl.prm.sched == nullptr) cl.prm.sched = host_sched_slot(h);
   void *args[] = {&cl.prm};
   IR_CUDA(h, cudaLaunchKernel(cl.fn, dim3(cl.grid), dim3(kThreads), args, cl.smem, st));
   return IR_OK;
@@ -366,6 +377,8 @@ ir_status ir_filter_create(ir_filter **out, int device) {
   IR_CUDA(nullptr, cudaMalloc(&h->d_launches, sizeof(unsigned long long)));
   IR_CUDA(nullptr, cudaMemset(h->d_status, 0, sizeof(unsigned)));
   IR_CUDA(nullptr, cudaMemset(h->d_launches, 0, sizeof(unsigned long long)));
+  IR_CUDA(nullptr, cudaMalloc(&h->d_sched, 2 * sizeof(unsigned) * kSchedSlots));
+  IR_CUDA(nullptr, cudaMemset(h->d_sched, 0, 2 * sizeof(unsigned) * kSchedSlots));
   for (int e = 1; e <= 2; ++e)
     for (int k = 3; k <= kMaxK; k += 2) h->cfg[e - 1][kslot(k)] = default_config(e, k);
   *out = h.release();
@@ -382,6 +395,7 @@ void ir_filter_destroy(ir_filter *h) {
   if (h->scratch) cudaFree(h->scratch);
   if (h->d_status) cudaFree(h->d_status);
   if (h->d_launches) cudaFree(h->d_launches);
+  if (h->d_sched) cudaFree(h->d_sched);
   delete h;
 }
 
@@ -569,7 +583,12 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
   }
   IR_CUDA(h, cudaMalloc(&plan->d_table, sizeof(FrameDev) * n));
   IR_CUDA(h, cudaMemcpy(plan->d_table, host.data(), sizeof(FrameDev) * n, cudaMemcpyHostToDevice));
-  for (size_t c = 0; c < plan->classes.size(); ++c) plan->classes[c].prm.table = plan->d_table + ranges[c].first;
+  IR_CUDA(h, cudaMalloc(&plan->d_sched, 2 * sizeof(unsigned) * plan->classes.size()));
+  IR_CUDA(h, cudaMemset(plan->d_sched, 0, 2 * sizeof(unsigned) * plan->classes.size()));
+  for (size_t c = 0; c < plan->classes.size(); ++c) {
+    plan->classes[c].prm.table = plan->d_table + ranges[c].first;
+    plan->classes[c].prm.sched = plan->d_sched + 2 * c;
+  }
 
   // explicit graph: counter memsets first, then one kernel node per class
   IR_CUDA(h, cudaGraphCreate(&plan->graph, 0));
@@ -626,6 +645,7 @@ void ir_batch_plan_destroy(ir_batch_plan *plan) {
   if (plan->exec) cudaGraphExecDestroy(plan->exec);
   if (plan->graph) cudaGraphDestroy(plan->graph);
   if (plan->d_table) cudaFree(plan->d_table);
+  if (plan->d_sched) cudaFree(plan->d_sched);
   delete plan;
 }
 

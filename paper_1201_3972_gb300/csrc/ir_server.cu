@@ -167,6 +167,7 @@ ir_status launch_batch(ir_server *s, Lane &L) {
     prm.table = L.d_table + lc.first;
     prm.nframes = lc.count;
     prm.total_tiles = lc.tiles;
+    prm.sched = host_sched_slot(h);
     const int grid = std::max(1, std::min(lc.tiles, lc.ci->max_grid));
     void *args[] = {&prm};
     if (cudaLaunchKernel(lc.ci->fn, dim3(grid), dim3(kThreads), args, lc.ci->smem, L.stream) != cudaSuccess) {

@@ -131,6 +131,33 @@ def test_every_algo_and_tile_random(flt, k, es):
     flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
 
 
+@pytest.mark.parametrize("k", [11, 15, 21])
+@pytest.mark.parametrize("es", [1, 2])
+def test_bitplane_sparse_and_dense_strips(flt, k, es):
+    """The bit-plane strategy selects per pixel across the warp in strips with
+    few flagged pixels and through bit planes otherwise: a smooth plateaued
+    field with rare impulses (few flagged per strip, many tied values in each
+    window), the same with dense impulses, and the two mixed in one frame."""
+    rng = np.random.default_rng(77 * k + es)
+    dt = _lib.IR_U8 if es == 1 else _lib.IR_U14
+    npdt = np.uint8 if es == 1 else np.uint16
+    maxv = 255 if es == 1 else 16383
+    H, W = 150, 203
+    y, x = np.mgrid[0:H, 0:W]
+    base = ((x + 2 * y) // 7 * (maxv // 90)) % (maxv // 2) + maxv // 8
+    flt.set_config(dt, k, 64, 64, _lib.IR_ALGO_BITPLANE)
+    for p in (0.002, 0.3):
+        a = base.copy()
+        m = rng.random((H, W)) < p
+        a[m] = rng.integers(0, maxv + 1, int(m.sum()))
+        check(flt, a.astype(npdt), k, u14=(es == 2))
+    a = base.copy()
+    m = (rng.random((H, W)) < 0.3) & (x < W // 2)
+    a[m] = rng.choice([0, maxv], int(m.sum()))
+    check(flt, a.astype(npdt), k, u14=(es == 2))
+    flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
 @pytest.mark.parametrize("k", [3, 5, 7, 9, 15, 21])
 def test_edge_shapes(flt, k):
     """1x1, single rows and columns, frames smaller than the window, odd
