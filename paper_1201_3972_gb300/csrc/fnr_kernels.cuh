@@ -1017,7 +1017,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
         fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
                            p.border, lane);
-      if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
+      // this warp's store from the same output tile (two tiles ago, or the
+      // previous tile when there is one output tile) has read its strip
+      if (lane == 0) {
+        if constexpr (out_buffers(ALGO) == 2) bulk_wait_read<1>();
+        else bulk_wait_read<0>();
+      }
       __syncwarp();
       int flagged = 0;
       {

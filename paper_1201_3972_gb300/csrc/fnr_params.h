@@ -72,6 +72,7 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
 // Staging buffers per CTA (a ring: the producer loads up to this many tiles
 // ahead of the slowest consumer warp).
 __host__ __device__ constexpr int num_stages(int algo) { return algo == ALGO_DENSE3 ? 3 : 2; }
+__host__ __device__ constexpr int out_buffers(int algo) { return algo == ALGO_BITPLANE ? 1 : 2; }
 constexpr int kMaxStages = 3;
 
 // Rows per vertical/horizontal extreme group of the compacted strategies.
@@ -134,8 +135,15 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
     L.off_stage[i] = off;
     if (i < num_stages(algo)) off += stage;
   }
+  // output tiles: two, alternating by tile, except for the bit-plane strategy,
+  // whose shared memory is the tightest (its warps wait for their previous
+  // store instead)
   L.off_out[0] = off; off += outb;
-  L.off_out[1] = off; off += outb;
+  L.off_out[1] = L.off_out[0];
+  if (out_buffers(algo) == 2) {
+    L.off_out[1] = off;
+    off += outb;
+  }
   L.w_list = L.w_vmin = L.w_vmax = L.w_planes = -1;
   int w = 0;
   if (algo != ALGO_DENSE3) {
@@ -144,7 +152,11 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
     L.w_vmax = w; w += align_up(L.sr * L.nps * 4, 16);
   }
   if (algo == ALGO_BITPLANE) {
-    L.w_planes = w; w += align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);
+    // the planes are built after the horizontal pass has consumed the extreme
+    // words, so they overlay them
+    const int planes = align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);
+    L.w_planes = L.w_vmin;
+    if (L.w_planes + planes > w) w = L.w_planes + planes;
   }
   L.warp_bytes = align_up(w, 128);
   L.off_warp = off; off += kConsumerWarps * L.warp_bytes;

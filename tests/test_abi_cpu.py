@@ -179,3 +179,73 @@ def test_dense3_identity_zero_one():
         med = sorted([max(lo), sorted(md)[1], min(hi)])[1]
         assert med == sorted(w)[4]
         assert min(lo) == min(w) and max(hi) == max(w)
+
+
+def test_shared_memory_layout_regions_are_disjoint():
+    """Every region of the kernel's shared-memory layout (stages, output tiles,
+    per-warp blocks, barriers, tile records, frame directory) lies inside the
+    total and overlaps no other, for every strategy, window and tile shape the
+    library accepts; the layout function is compiled from the kernel header."""
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = r'''
+#include <cstdio>
+#include "fnr_params.h"
+using namespace fnr;
+static bool overlap(long a0, long a1, long b0, long b1) { return a0 < b1 && b0 < a1; }
+int main() {
+  int bad = 0, n = 0;
+  for (int es = 1; es <= 2; ++es)
+    for (int k = 3; k <= kMaxK; k += 2)
+      for (int algo = ALGO_DENSE3; algo <= ALGO_BITPLANE; ++algo) {
+        if (algo == ALGO_DENSE3 && k != 3) continue;
+        if (algo == ALGO_NETWORK && k > 9) continue;
+        for (int tw = 8; tw <= 256; tw += 8)
+          for (int th = 8; th <= 256; th += 8) {
+            if ((tw * es) % 16 || th % tile_h_multiple(k, algo)) continue;
+            const Layout L = make_layout(es, k, algo, th, tw);
+            if (L.bw > 256 || L.bh > 256) continue;
+            ++n;
+            long r[16][2]; int m = 0;
+            const long stage = L.off_stage[1] - L.off_stage[0];
+            for (int s = 0; s < num_stages(algo); ++s) { r[m][0] = L.off_stage[0] + s * stage; r[m][1] = r[m][0] + (long)L.bw * L.bh * es; ++m; }
+            const long outb = algo == ALGO_DENSE3 ? 0 : (long)tw * th * es;
+            for (int o = 0; o < out_buffers(algo); ++o) { r[m][0] = L.off_out[o]; r[m][1] = r[m][0] + outb; ++m; }
+            if (out_buffers(algo) == 1 && L.off_out[1] != L.off_out[0]) ++bad;
+            r[m][0] = L.off_warp; r[m][1] = L.off_warp + (long)kConsumerWarps * L.warp_bytes; ++m;
+            r[m][0] = L.off_bar; r[m][1] = L.off_bar + 16 * kMaxStages; ++m;
+            r[m][0] = L.off_info; r[m][1] = L.off_info + 32 * kMaxStages; ++m;
+            r[m][0] = L.off_dir; r[m][1] = L.off_dir + kDirMax * 4; ++m;
+            for (int i = 0; i < m; ++i) {
+              if (r[i][0] < 0 || r[i][1] > L.total) ++bad;
+              for (int j = i + 1; j < m; ++j)
+                if (r[i][1] > r[i][0] && r[j][1] > r[j][0] && overlap(r[i][0], r[i][1], r[j][0], r[j][1])) ++bad;
+            }
+            if (algo != ALGO_DENSE3) {  // inside a warp block: list, then extremes (planes overlay them)
+              const long list1 = L.w_list + (long)L.sr * tw * 2, v0 = L.w_vmin, v1 = L.w_vmax + (long)L.sr * L.nps * 4;
+              if (overlap(L.w_list, list1, v0, v1) || v1 > L.warp_bytes) ++bad;
+              if (algo == ALGO_BITPLANE) {
+                const long p1 = L.w_planes + (long)L.nbmax * L.plane_rows * L.pw * 4;
+                if (overlap(L.w_list, list1, L.w_planes, p1) || p1 > L.warp_bytes) ++bad;
+              }
+            }
+          }
+      }
+  printf("%d %d\n", n, bad);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "lay.cpp")
+        exe = os.path.join(d, "lay")
+        with open(c, "w") as fh:
+            fh.write(src)
+        cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+        r = subprocess.run(["g++", "-std=c++17", "-D__host__=", "-D__device__=", "-I",
+                            os.path.join(root, "paper_1201_3972_gb300", "csrc"), "-I", os.path.join(root, "include"),
+                            "-I", cuda_inc, "-o", exe, c], capture_output=True, text=True)
+        if r.returncode != 0:
+            pytest.skip("no host compiler for the layout check: " + r.stderr[-300:])
+        n, bad = map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split())
+    assert n > 100 and bad == 0
