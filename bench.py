@@ -399,7 +399,7 @@ def serve_leg(args, device):
     streams = synth.workload_serve(streams=64, pool=args.serve_pool)
     pools = serve.make_pools(streams)
     ref = serve.reference_hashes(pools, streams, device)
-    live = serve.simulate(streams, args.serve_seconds, pools, ref, verify_every=8, device=device)
+    live = serve.simulate(streams, args.serve_seconds, pools, ref, verify_every=1, device=device)
     sat_s = min(3.0, args.serve_seconds)
     sat = serve.drive(streams, pools, sat_s, inflight=4, device=device)
     plain = serve.drive(streams, pools, sat_s, plain=True, device=device)
