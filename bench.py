@@ -303,6 +303,8 @@ def own_arm(args):
         "gpu_launches": int(gpu_launches), "launches_per_step": launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
+    if rank == 0:
+        result["single_frame"] = single_frame_leg(flt, stream, args)
     if rank == 0 and not args.no_batch_leg:
         result["batch_mixed"] = batch_leg(flt, stream, args)
     if rank == 0 and not args.no_large_k:
@@ -352,6 +354,37 @@ def batch_leg(flt, stream, args):
                      "kernels_per_launch": plan.kernel_count}
         plan.close()
     return out
+
+
+def single_frame_leg(flt, stream, args):
+    """One 320x240 u8 frame, 10% salt-and-pepper, k = 3, one ir_filter_run2
+    call per frame: launch-latency bound, so reported in microseconds (device
+    time between events around the call, and host wall time of the call with
+    its synchronisation)."""
+    import torch
+    from paper_1201_3972_gb300 import _lib, synth
+    s = synth.workload_single_u8()[0]
+    f = s.make()
+    src = torch.from_numpy(f).cuda()
+    dst = torch.empty_like(src)
+    H, W = f.shape
+
+    def once():
+        flt.ir_filter_run2(int(src.data_ptr()), W, int(dst.data_ptr()), W, H, W, _lib.IR_U8, 3,
+                           stream.cuda_stream, None)
+    for _ in range(max(3, args.warmup)):
+        once()
+    dev_us = 1e3 * statistics.median(time_events(torch, once, 50, stream))
+    torch.cuda.synchronize()
+    walls = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        once()
+        stream.synchronize()
+        walls.append(time.perf_counter() - t0)
+    wall_us = 1e6 * statistics.median(walls)
+    return {"frame": "320x240 u8, 10% salt-and-pepper, k=3", "device_us": round(dev_us, 2),
+            "wall_us": round(wall_us, 2), "mpx_s": round(H * W / dev_us, 1)}
 
 
 def large_k_leg(flt, stream, args):
