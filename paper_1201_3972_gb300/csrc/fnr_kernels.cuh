@@ -663,9 +663,11 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
   return base;
 }
 
-// Flagged pixels of the strip, two per lane: the two k x k windows are
-// gathered into the low and high 16-bit lanes of the same registers and one
-// packed selection network serves both (an odd tail pixel pairs with itself).
+// The medians of two flagged pixels, at stage-window rows ya / yb (tile row
+// of the output pixel; the window spans stage rows ya .. ya + K - 1) and tile
+// columns xa / xb, gathered into the low and high 16-bit lanes of the same
+// registers so that one packed selection network serves both; the results go
+// to the output tile.
 //
 // 16-bit pixels are gathered as 32-bit words: a window row of K = 2R+1
 // pixels always lies in R+1 aligned words, whose 2R+2 halves hold the row
@@ -676,50 +678,95 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
 // per-pixel selector. The network does not care in which order a window's
 // values arrive, only that each register holds one value of each pixel.
 template <typename T, int K>
-__device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane,
-                              PackedOp op) {
+__device__ __forceinline__ void median_pair(const T *S, T *O, int TW, int BW, int ya, int xa, int yb, int xb,
+                                            PackedOp op) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
+  uint32_t v[K * K];
+  if constexpr (sizeof(T) == 2) {
+    const uint32_t *W32 = reinterpret_cast<const uint32_t *>(S);
+    const int BWW = BW >> 1;  // BW is even: rows start on a word
+    const int sa = ya * BW + (XOFF - R) + xa, sb = yb * BW + (XOFF - R) + xb;
+    const uint32_t *wa = W32 + (sa >> 1), *wb = W32 + (sb >> 1);
+    // leftover pixel: low half of word 0 (even start) or high half of word R (odd start)
+    const uint32_t sel_a = (sa & 1) ? 0x0076u : 0x0010u;
+    const uint32_t sel_b = (sb & 1) ? 0x7600u : 0x1000u;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      uint32_t ua[R + 1], ub[R + 1];
+#pragma unroll
+      for (int t = 0; t <= R; ++t) {
+        ua[t] = wa[a * BWW + t];
+        ub[t] = wb[a * BWW + t];
+      }
+#pragma unroll
+      for (int h = 1; h <= 2 * R; ++h)
+        v[a * K + h - 1] = __byte_perm(ua[h >> 1], ub[h >> 1], (h & 1) ? 0x7632u : 0x5410u);
+      v[a * K + 2 * R] = __byte_perm(__byte_perm(ua[0], ua[R], sel_a), __byte_perm(ub[0], ub[R], sel_b), 0x7610u);
+    }
+  } else {
+    const T *ba = S + ya * BW + (XOFF - R) + xa;
+    const T *bb = S + yb * BW + (XOFF - R) + xb;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < K; ++b)
+        v[a * K + b] = __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
+  }
+  const uint32_t m = MedianNet<K>::run(v, op);
+  O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
+  O[yb * TW + xb] = static_cast<T>(m >> 16);
+}
+
+// The flagged pixels of the warp's strip, two per lane.
+template <typename T, int K>
+__device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int TW, int BW, int r0, int lane,
+                              PackedOp op) {
   const int pairs = (F + 1) >> 1;
   for (int i = lane; i < pairs; i += 32) {
     const int ea = list[2 * i];
     const int eb = 2 * i + 1 < F ? list[2 * i + 1] : ea;
-    const int ya = r0 + (ea >> 8), xa = ea & 255, yb = r0 + (eb >> 8), xb = eb & 255;
-    uint32_t v[K * K];
-    if constexpr (sizeof(T) == 2) {
-      const uint32_t *W32 = reinterpret_cast<const uint32_t *>(S);
-      const int BWW = BW >> 1;  // BW is even: rows start on a word
-      const int sa = ya * BW + (XOFF - R) + xa, sb = yb * BW + (XOFF - R) + xb;
-      const uint32_t *wa = W32 + (sa >> 1), *wb = W32 + (sb >> 1);
-      // leftover pixel: low half of word 0 (even start) or high half of word R (odd start)
-      const uint32_t sel_a = (sa & 1) ? 0x0076u : 0x0010u;
-      const uint32_t sel_b = (sb & 1) ? 0x7600u : 0x1000u;
+    median_pair<T, K>(S, O, TW, BW, r0 + (ea >> 8), ea & 255, r0 + (eb >> 8), eb & 255, op);
+  }
+}
+
+// Whether the network strategy pools the flagged pixels of a tile across its
+// strips (network_pooled). Pooling saves the partial round each strip would
+// run on its own but synchronises the tile's warps twice; measured on GB300
+// it pays for the 81-input network of k = 9 (67 against 80 us per eight
+// 1280x1024 frames with 3.5% flagged pixels), is even for k = 7 and loses
+// for k = 5 (273 against 297 Gpx/s), where a round is cheap.
+template <int K>
+struct PoolMedians {
+  static constexpr bool value = K >= 9;
+};
+
+// The flagged pixels of the whole tile, pooled: the warps' lists, in warp
+// order, form one sequence; pair p takes its entries 2p and 2p + 1 (an odd
+// last entry pairs with itself) and round r of 32 pairs goes to warp
+// r mod 8. A strip alone would run a partial round of its own; pooled, the
+// tile runs ceil(pairs / 32) rounds in all. counts[w] is the length of warp
+// w's list, total their sum; list entries are (row in strip << 8 | column).
+template <typename T, int K>
+__device__ void network_pooled(const T *S, T *O, const unsigned char *warp_blocks, int warp_bytes, int w_list,
+                               const int *counts, int total, int TW, int BW, int SR, int warp, int lane,
+                               PackedOp op) {
+  const int pairs = (total + 1) >> 1;
+  for (int pi = warp * 32 + lane; pi - lane < pairs; pi += 32 * kConsumerWarps) {
+    if (pi >= pairs) continue;
+    const int ga = 2 * pi, gb = 2 * pi + 1 < total ? 2 * pi + 1 : ga;
+    // the list each entry lives in, from the counts in shared memory (kept
+    // out of registers: they would be live across the network)
+    int wa = 0, wb = 0, base_a = 0, base_b = 0, pre = 0;
 #pragma unroll
-      for (int a = 0; a < K; ++a) {
-        uint32_t ua[R + 1], ub[R + 1];
-#pragma unroll
-        for (int t = 0; t <= R; ++t) {
-          ua[t] = wa[a * BWW + t];
-          ub[t] = wb[a * BWW + t];
-        }
-#pragma unroll
-        for (int h = 1; h <= 2 * R; ++h)
-          v[a * K + h - 1] = __byte_perm(ua[h >> 1], ub[h >> 1], (h & 1) ? 0x7632u : 0x5410u);
-        v[a * K + 2 * R] = __byte_perm(__byte_perm(ua[0], ua[R], sel_a), __byte_perm(ub[0], ub[R], sel_b), 0x7610u);
-      }
-    } else {
-      const T *ba = S + ya * BW + (XOFF - R) + xa;
-      const T *bb = S + yb * BW + (XOFF - R) + xb;
-#pragma unroll
-      for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int b = 0; b < K; ++b)
-          v[a * K + b] =
-              __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
+    for (int j = 1; j < kConsumerWarps; ++j) {
+      pre += counts[j - 1];
+      if (ga >= pre) { wa = j; base_a = pre; }
+      if (gb >= pre) { wb = j; base_b = pre; }
     }
-    const uint32_t m = MedianNet<K>::run(v, op);
-    O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
-    O[yb * TW + xb] = static_cast<T>(m >> 16);
+    const int ea = reinterpret_cast<const uint16_t *>(warp_blocks + wa * warp_bytes + w_list)[ga - base_a];
+    const int eb = reinterpret_cast<const uint16_t *>(warp_blocks + wb * warp_bytes + w_list)[gb - base_b];
+    median_pair<T, K>(S, O, TW, BW, wa * SR + (ea >> 8), ea & 255, wb * SR + (eb >> 8), eb & 255, op);
   }
 }
 
@@ -893,6 +940,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   T *const out1 = reinterpret_cast<T *>(smem + L.off_out[1]);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bar);  // [NS]: tile staged
   uint64_t *empty = full + NS;                                       // [NS]: all consumers done with it
+  uint64_t *pooled = reinterpret_cast<uint64_t *>(smem + L.off_sync);  // [NS]: network: lists complete
+  uint64_t *stored = pooled + kMaxStages;                              // [NS]: network: medians written
+  int *counts = reinterpret_cast<int *>(smem + L.off_sync + 16 * kMaxStages);  // [NS][warps]: list lengths
   TileInfo *info = reinterpret_cast<TileInfo *>(smem + L.off_info);  // [stage]: tile staged there
   int *dir = reinterpret_cast<int *>(smem + L.off_dir);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -903,6 +953,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
+      mbar_init(&pooled[s], kConsumerWarps * 32);  // every consumer lane arrives (releasing its own writes)
+      mbar_init(&stored[s], kConsumerWarps * 32);
     }
     fence_mbar_init();
     if (blockIdx.x == 0 && p.launches != nullptr) atomicAdd(p.launches, 1ull);
@@ -1012,6 +1064,57 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       } else {
         dense3_strip<T, false, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
                                       lane, flagged, d3op);
+      }
+    } else if constexpr (ALGO == ALGO_NETWORK && PoolMedians<K>::value) {
+      // Every consumer warp takes part, live strip or not: the strips' flagged
+      // pixels are pooled across the tile (network_pooled), between two
+      // CTA-level points, both mbarriers with bounded waits: `pooled` (every
+      // list and its fix-up rows are complete) and `stored` (every median is
+      // in the output tile and fenced for the TMA store).
+      uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
+      int flagged = 0;
+      if (live && tma_in && p.border != kBorderZero &&
+          (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
+        fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
+                           p.border, lane);
+      if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
+      __syncwarp();
+      if (live) {
+        uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
+        uint32_t *vmax = reinterpret_cast<uint32_t *>(wbase + L.w_vmax);
+        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
+        __syncwarp();
+        flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
+                                         p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
+      }
+      if (lane == 0) counts[s * kConsumerWarps + warp] = flagged;
+      __syncwarp();
+      mbar_arrive(&pooled[s]);
+      if (!mbar_wait_bounded(&pooled[s], (i / NS) & 1u, kWaitCycles)) {
+        if (lane == 0) atomicOr(p.status, kStatusTimeout);
+        break;
+      }
+      int total = 0;
+#pragma unroll
+      for (int j = 0; j < kConsumerWarps; ++j) total += counts[s * kConsumerWarps + j];
+      network_pooled<T, K>(S, O, smem + L.off_warp, L.warp_bytes, L.w_list, counts + s * kConsumerWarps, total, TW,
+                           BW, SR, warp, lane, PackedOp{p.unit, 0u - p.unit});
+      fence_proxy_async_smem();  // the medians written here precede every warp's TMA store of its strip
+      mbar_arrive(&stored[s]);
+      if (!mbar_wait_bounded(&stored[s], (i / NS) & 1u, kWaitCycles)) {
+        if (lane == 0) atomicOr(p.status, kStatusTimeout);
+        break;
+      }
+      if (live) {
+        if (tma_out) {
+          if (lane == 0) tma_store_2d(&cf->tout, O + r0 * TW, x0, y0 + r0);
+        } else {
+          plain_strip_store<T>(cf, O, x0, y0, TW, r0, SR, lane);
+        }
+      }
+      if (lane == 0) {
+        bulk_commit();  // one bulk group per tile (empty for a strip outside the frame)
+        if (flagged != 0 && cur.counted) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       }
     } else if (live) {
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))

@@ -98,6 +98,7 @@ struct Layout {
   int w_list, w_vmin, w_vmax, w_planes;  // offsets inside a per-warp block
   int plane_rows;      // rows of bit planes a warp builds (its strip + halo)
   int off_bar;         // full[stages], empty[stages]
+  int off_sync;        // network strategy: pooled[stages], stored[stages] barriers, then list counts [stages][warps]
   int off_info;
   int off_dir;
   int total;
@@ -161,6 +162,7 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   L.warp_bytes = align_up(w, 128);
   L.off_warp = off; off += kConsumerWarps * L.warp_bytes;
   L.off_bar = off; off += 16 * kMaxStages;
+  L.off_sync = off; off += 16 * kMaxStages + 4 * kConsumerWarps * kMaxStages;
   L.off_info = off; off += 32 * kMaxStages;
   L.off_dir = off; off += kDirMax * 4;
   L.total = align_up(off, 128);

@@ -207,7 +207,7 @@ int main() {
             const Layout L = make_layout(es, k, algo, th, tw);
             if (L.bw > 256 || L.bh > 256) continue;
             ++n;
-            long r[16][2]; int m = 0;
+            long r[20][2]; int m = 0;
             const long stage = L.off_stage[1] - L.off_stage[0];
             for (int s = 0; s < num_stages(algo); ++s) { r[m][0] = L.off_stage[0] + s * stage; r[m][1] = r[m][0] + (long)L.bw * L.bh * es; ++m; }
             const long outb = algo == ALGO_DENSE3 ? 0 : (long)tw * th * es;
@@ -217,6 +217,7 @@ int main() {
             r[m][0] = L.off_bar; r[m][1] = L.off_bar + 16 * kMaxStages; ++m;
             r[m][0] = L.off_info; r[m][1] = L.off_info + 32 * kMaxStages; ++m;
             r[m][0] = L.off_dir; r[m][1] = L.off_dir + kDirMax * 4; ++m;
+            r[m][0] = L.off_sync; r[m][1] = L.off_sync + 16 * kMaxStages + 4 * kConsumerWarps * kMaxStages; ++m;
             for (int i = 0; i < m; ++i) {
               if (r[i][0] < 0 || r[i][1] > L.total) ++bad;
               for (int j = i + 1; j < m; ++j)
