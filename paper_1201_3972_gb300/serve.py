@@ -217,7 +217,11 @@ def simulate(streams: Sequence[synth.StreamSpec], duration_s: float, pools: Pool
         vlock = threading.Lock()
 
         def verifier():
-            scratch = {si: np.empty(pools.frames[si][0].shape, np.uint16) for si in pools.frames}
+            # pinned read-back buffers: the copies then neither stage through
+            # driver buffers nor hold the host thread longer than the transfer
+            import torch
+            scratch = {si: torch.empty(pools.frames[si][0].shape, dtype=torch.int16, pin_memory=True).numpy()
+                       .view(np.uint16) for si in pools.frames}
             nonlocal verified, mismatches
             while True:
                 item = vq.get()
@@ -235,17 +239,21 @@ def simulate(streams: Sequence[synth.StreamSpec], duration_s: float, pools: Pool
                     if keep_outputs:
                         outputs[(sid, j)] = buf.copy()
                 srv.release(sids[sid], slot)
+                if closed_loop and srv.clock() < deadline:
+                    closed_submit(s)  # the stream's next frame, once its slot is back
                 vq.task_done()
 
-        verifiers = [threading.Thread(target=verifier, daemon=True) for _ in range(6)] if ref is not None else []
+        deadline = t0 + duration_s
+        verifiers = [threading.Thread(target=verifier, daemon=True) for _ in range(3)] if ref is not None else []
         for v in verifiers:
             v.start()
 
         def closed_submit(s):
-            tag = tag_counter[0]
-            tag_counter[0] += 1
-            j = next_j[s.stream_id]
-            next_j[s.stream_id] = j + 1
+            with lock:
+                tag = tag_counter[0]
+                tag_counter[0] += 1
+                j = next_j[s.stream_id]
+                next_j[s.stream_id] = j + 1
             return submit(s, j, srv.clock(), tag)
 
         if closed_loop:
@@ -257,7 +265,6 @@ def simulate(streams: Sequence[synth.StreamSpec], duration_s: float, pools: Pool
             th = threading.Thread(target=producer, daemon=True)
             th.start()
         t_start = srv.clock()
-        deadline = t0 + duration_s
         n_done = 0
         while True:
             comps = srv.poll()
@@ -269,13 +276,15 @@ def simulate(streams: Sequence[synth.StreamSpec], duration_s: float, pools: Pool
                 done_px += s.H * s.W
                 n_done += 1
                 if ref is not None and verify_every and n_done % verify_every == 0:
-                    vq.put((sid, c.slot, j))  # the verifier releases the slot
+                    vq.put((sid, c.slot, j))  # the verifier releases the slot (and resubmits in closed loop)
                 else:
                     srv.release(sids[sid], c.slot)
-                if closed_loop and srv.clock() < deadline:
-                    closed_submit(s)
+                    if closed_loop and srv.clock() < deadline:
+                        closed_submit(s)
             if closed_loop:
-                if srv.clock() >= deadline and not arrivals:
+                # a verifier marks its item done only after resubmitting, so
+                # an empty queue and no arrivals mean nothing more will come
+                if srv.clock() >= deadline and not arrivals and vq.unfinished_tasks == 0:
                     break
             elif producer_done.is_set() and not arrivals:
                 break
