@@ -738,7 +738,7 @@ __device__ void network_strip(const T *S, T *O, const uint16_t *list, int F, int
 // for k = 5 (273 against 297 Gpx/s), where a round is cheap.
 template <int K>
 struct PoolMedians {
-  static constexpr bool value = K >= 9;
+  static constexpr bool value = pool_medians(ALGO_NETWORK, K);
 };
 
 // The flagged pixels of the whole tile, pooled: the warps' lists, in warp
@@ -941,7 +941,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bar);  // [NS]: tile staged
   uint64_t *empty = full + NS;                                       // [NS]: all consumers done with it
   uint64_t *pooled = reinterpret_cast<uint64_t *>(smem + L.off_sync);  // [NS]: network: lists complete
-  uint64_t *stored = pooled + kMaxStages;                              // [NS]: network: medians written
   int *counts = reinterpret_cast<int *>(smem + L.off_sync + 16 * kMaxStages);  // [NS][warps]: list lengths
   TileInfo *info = reinterpret_cast<TileInfo *>(smem + L.off_info);  // [stage]: tile staged there
   int *dir = reinterpret_cast<int *>(smem + L.off_dir);
@@ -954,7 +953,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kConsumerWarps);
       mbar_init(&pooled[s], kConsumerWarps * 32);  // every consumer lane arrives (releasing its own writes)
-      mbar_init(&stored[s], kConsumerWarps * 32);
     }
     fence_mbar_init();
     if (blockIdx.x == 0 && p.launches != nullptr) atomicAdd(p.launches, 1ull);
@@ -1020,6 +1018,25 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   const FastDiv divNP(static_cast<uint32_t>(L.np));     // compacted: vertical items per row group
   const FastDiv divG(static_cast<uint32_t>(TW / 8));    // compacted: horizontal items per row
   unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;
+  // pooled network strategy: this warp's strip of the previous tile, stored
+  // after the next pooling point (one bulk group per call)
+  struct PrevStrip {
+    const FrameDev *cf;
+    int x0, y0;
+    bool live, tma_out;
+    T *O;
+  } prev{nullptr, 0, 0, false, false, nullptr};
+  auto store_prev = [&]() {
+    if (prev.live) {
+      if (prev.tma_out) {
+        if (lane == 0) tma_store_2d(&prev.cf->tout, prev.O + r0 * TW, prev.x0, prev.y0 + r0);
+      } else {
+        plain_strip_store<T>(prev.cf, prev.O, prev.x0, prev.y0, TW, r0, SR, lane);
+      }
+    }
+    if (lane == 0) bulk_commit();
+    prev.live = false;
+  };
   for (int i = 0;; ++i) {
     const int s = i % NS;
     if (!mbar_wait_bounded(&full[s], (i / NS) & 1u, kWaitCycles)) {
@@ -1027,7 +1044,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       break;
     }
     const TileInfo cur = info[s];
-    if (!cur.valid) break;
+    if (!cur.valid) {
+      if constexpr (ALGO == ALGO_NETWORK && PoolMedians<K>::value) {
+        // the end: once every warp is here, the last tile's medians are all written
+        mbar_arrive(&pooled[s]);
+        if (mbar_wait_bounded(&pooled[s], (i / NS) & 1u, kWaitCycles)) store_prev();
+        else if (lane == 0) atomicOr(p.status, kStatusTimeout);
+      }
+      break;
+    }
     const FrameDev *cf = frame_ptr(p, cur.f);
     const int x0 = cur.x0, y0 = cur.y0;
     const int xs = x0 - XOFF, ys = y0 - R;
@@ -1067,17 +1092,21 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       }
     } else if constexpr (ALGO == ALGO_NETWORK && PoolMedians<K>::value) {
       // Every consumer warp takes part, live strip or not: the strips' flagged
-      // pixels are pooled across the tile (network_pooled), between two
-      // CTA-level points, both mbarriers with bounded waits: `pooled` (every
-      // list and its fix-up rows are complete) and `stored` (every median is
-      // in the output tile and fenced for the TMA store).
-      uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
+      // pixels are pooled across the tile (network_pooled) after one CTA-level
+      // point per tile, an mbarrier with a bounded wait (`pooled`): every list
+      // of this tile and its fix-up rows are complete, and every median of the
+      // previous tile is written and fenced, so the strips of the previous
+      // tile are stored right after it (its output tile is the other one).
+      const int w_list = L.w_list + (i & 1) * L.list_bytes;  // this tile's list (see pool_medians)
+      uint16_t *list = reinterpret_cast<uint16_t *>(wbase + w_list);
       int flagged = 0;
       if (live && tma_in && p.border != kBorderZero &&
           (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
         fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
                            p.border, lane);
-      if (lane == 0) bulk_wait_read<1>();  // this warp's store from O two tiles ago has read its strip
+      // the store issued during the previous tile (of the tile before it, from
+      // this output tile) has read its strip
+      if (lane == 0) bulk_wait_read<0>();
       __syncwarp();
       if (live) {
         uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
@@ -1087,35 +1116,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
                                          p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
       }
-      if (lane == 0) counts[s * kConsumerWarps + warp] = flagged;
+      if (lane == 0) {
+        counts[s * kConsumerWarps + warp] = flagged;
+        if (flagged != 0 && cur.counted) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
+      }
       __syncwarp();
       mbar_arrive(&pooled[s]);
       if (!mbar_wait_bounded(&pooled[s], (i / NS) & 1u, kWaitCycles)) {
         if (lane == 0) atomicOr(p.status, kStatusTimeout);
         break;
       }
+      store_prev();
       int total = 0;
 #pragma unroll
       for (int j = 0; j < kConsumerWarps; ++j) total += counts[s * kConsumerWarps + j];
-      network_pooled<T, K>(S, O, smem + L.off_warp, L.warp_bytes, L.w_list, counts + s * kConsumerWarps, total, TW,
-                           BW, SR, warp, lane, PackedOp{p.unit, 0u - p.unit});
-      fence_proxy_async_smem();  // the medians written here precede every warp's TMA store of its strip
-      mbar_arrive(&stored[s]);
-      if (!mbar_wait_bounded(&stored[s], (i / NS) & 1u, kWaitCycles)) {
-        if (lane == 0) atomicOr(p.status, kStatusTimeout);
-        break;
-      }
-      if (live) {
-        if (tma_out) {
-          if (lane == 0) tma_store_2d(&cf->tout, O + r0 * TW, x0, y0 + r0);
-        } else {
-          plain_strip_store<T>(cf, O, x0, y0, TW, r0, SR, lane);
-        }
-      }
-      if (lane == 0) {
-        bulk_commit();  // one bulk group per tile (empty for a strip outside the frame)
-        if (flagged != 0 && cur.counted) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
-      }
+      network_pooled<T, K>(S, O, smem + L.off_warp, L.warp_bytes, w_list, counts + s * kConsumerWarps, total, TW, BW,
+                           SR, warp, lane, PackedOp{p.unit, 0u - p.unit});
+      fence_proxy_async_smem();  // these medians precede the TMA stores issued after the next pooling point
+      prev = PrevStrip{cf, x0, y0, live, tma_out, O};
     } else if (live) {
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
         fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,

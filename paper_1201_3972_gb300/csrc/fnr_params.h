@@ -73,6 +73,10 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
 // ahead of the slowest consumer warp).
 __host__ __device__ constexpr int num_stages(int algo) { return algo == ALGO_DENSE3 ? 3 : 2; }
 __host__ __device__ constexpr int out_buffers(int algo) { return algo == ALGO_BITPLANE ? 1 : 2; }
+// Whether the network strategy pools the flagged pixels of a tile across its
+// strips; a pooling warp keeps two flagged lists, alternating by tile, since
+// the other warps may still read its previous list while it builds the next.
+__host__ __device__ constexpr bool pool_medians(int algo, int k) { return algo == ALGO_NETWORK && k >= 9; }
 constexpr int kMaxStages = 3;
 
 // Rows per vertical/horizontal extreme group of the compacted strategies.
@@ -96,9 +100,10 @@ struct Layout {
   int off_warp;        // first per-warp block
   int warp_bytes;      // size of one per-warp block
   int w_list, w_vmin, w_vmax, w_planes;  // offsets inside a per-warp block
+  int list_bytes;                        // one flagged list (two when pooling, alternating by tile)
   int plane_rows;      // rows of bit planes a warp builds (its strip + halo)
   int off_bar;         // full[stages], empty[stages]
-  int off_sync;        // network strategy: pooled[stages], stored[stages] barriers, then list counts [stages][warps]
+  int off_sync;        // network strategy: pooled[stages] barriers (and a spare row), then list counts [stages][warps]
   int off_info;
   int off_dir;
   int total;
@@ -148,7 +153,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   L.w_list = L.w_vmin = L.w_vmax = L.w_planes = -1;
   int w = 0;
   if (algo != ALGO_DENSE3) {
-    L.w_list = w; w += align_up(L.sr * tile_w * 2, 16);
+    L.list_bytes = align_up(L.sr * tile_w * 2, 16);
+    L.w_list = w; w += L.list_bytes * (pool_medians(algo, k) ? 2 : 1);
     L.w_vmin = w; w += align_up(L.sr * L.nps * 4, 16);
     L.w_vmax = w; w += align_up(L.sr * L.nps * 4, 16);
   }

@@ -224,7 +224,9 @@ int main() {
                 if (r[i][1] > r[i][0] && r[j][1] > r[j][0] && overlap(r[i][0], r[i][1], r[j][0], r[j][1])) ++bad;
             }
             if (algo != ALGO_DENSE3) {  // inside a warp block: list, then extremes (planes overlay them)
-              const long list1 = L.w_list + (long)L.sr * tw * 2, v0 = L.w_vmin, v1 = L.w_vmax + (long)L.sr * L.nps * 4;
+              const long list1 = L.w_list + (long)L.list_bytes * (pool_medians(algo, k) ? 2 : 1);
+              const long v0 = L.w_vmin, v1 = L.w_vmax + (long)L.sr * L.nps * 4;
+              if (L.list_bytes < (long)L.sr * tw * 2) ++bad;
               if (overlap(L.w_list, list1, v0, v1) || v1 > L.warp_bytes) ++bad;
               if (algo == ALGO_BITPLANE) {
                 const long p1 = L.w_planes + (long)L.nbmax * L.plane_rows * L.pw * 4;
