@@ -770,57 +770,96 @@ __device__ void network_pooled(const T *S, T *O, const unsigned char *warp_block
   }
 }
 
-// Bit planes of the stage rows [r0, r0 + rows): plane b, row i, word w holds
-// bit b of the 32 pixels of row r0+i starting at column 32w. One ballot per
-// (row, word, bit). Returns the OR of all those pixels (warp-uniform).
+// Bit planes of the stage rows [r0, r0 + rows): word (bit b, row i, column
+// word w) at planes[(b * rows + i) * PW + w] holds bit b of the 32 pixels of
+// row r0 + i from column 32w. This order keeps the selection's reads, where
+// each lane reads its own pixel's rows at one bit, in distinct banks. One
+// ballot per (row, word, bit); the ballots of kPlaneGroup items go through
+// the warp's staging buffer (lane 0 writes them as 16-byte vectors, then
+// every lane moves two words into place). The last word of every row is zero
+// (a window segment may reach into it). Returns the OR of the pixels.
 template <typename T>
-__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int r0, int rows, int PW, int NBMAX,
+__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, uint32_t *stage, int BW, int r0, int rows, int PW,
                                       int lane) {
+  constexpr int NB = 8 * sizeof(T);
+  constexpr int G = kPlaneGroup;
   const int wpr = PW - 1;
+  const int items = rows * wpr;
   uint32_t orv = 0;
-  for (int it = 0; it < rows * wpr; ++it) {
-    const int row = it / wpr, w = it - row * wpr;
-    const int col = (w << 5) + lane;
-    const uint32_t v = col < BW ? static_cast<uint32_t>(S[(r0 + row) * BW + col]) : 0u;
-    orv |= v;
-    uint32_t mine = 0;
-    for (int b = 0; b < NBMAX; ++b) {
-      const uint32_t bits = __ballot_sync(0xffffffffu, (v >> b) & 1u);
-      if (lane == b) mine = bits;
+  for (int it0 = 0; it0 < items; it0 += G) {
+    uint32_t v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int it = it0 + g < items ? it0 + g : items - 1;  // a repeated item rewrites the same words
+      const int row = it / wpr, w = it - row * wpr;
+      const int col = (w << 5) + lane;
+      v[g] = col < BW ? static_cast<uint32_t>(S[(r0 + row) * BW + col]) : 0u;
+      orv |= v[g];
     }
-    if (lane < NBMAX) planes[(lane * rows + row) * PW + w] = mine;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      uint32_t bits[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) bits[b] = __ballot_sync(0xffffffffu, (v[g] >> b) & 1u);
+      if (lane == 0) {
+        uint4 *dst = reinterpret_cast<uint4 *>(stage + g * NB);
+#pragma unroll
+        for (int j = 0; j < NB / 4; ++j) dst[j] = make_uint4(bits[4 * j], bits[4 * j + 1], bits[4 * j + 2], bits[4 * j + 3]);
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int idx = lane; idx < G * NB; idx += 32) {
+      const int g = idx / NB, b = idx - g * NB;
+      const int it = it0 + g < items ? it0 + g : items - 1;
+      const int row = it / wpr, w = it - row * wpr;
+      planes[(b * rows + row) * PW + w] = stage[idx];
+    }
+    __syncwarp();
   }
-  for (int it = lane; it < NBMAX * rows; it += 32) planes[it * PW + wpr] = 0u;
+  for (int it = lane; it < NB * rows; it += 32) planes[it * PW + wpr] = 0u;
   __syncwarp();
   return __reduce_or_sync(0xffffffffu, orv);
 }
 
 // Flagged pixels of the strip: radix select on the window, most significant
-// bit first. alive[a] marks the window pixels of row a whose bits above the
-// current bit match the answer so far; each round counts the live pixels
-// with a 0 bit. Plane rows are relative to the strip's first stage row.
+// bit first. alive marks the window pixels whose bits above the current bit
+// match the answer so far; each round counts the live pixels with a 0 bit.
+// Plane rows are relative to the strip's first stage row. Windows up to 16
+// wide keep two rows per register (segments of rows 2j and 2j+1 in the low
+// and high halves), so one popcount serves both.
 template <typename T, int K>
 __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *list, int F, int TW, int rows, int PW,
                                int NB, int r0, int lane) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
   constexpr uint32_t kMask = (1u << K) - 1u;
+  constexpr bool kPack = K <= 16;
+  constexpr int NA = kPack ? (K + 1) / 2 : K;  // alive words
   for (int i = lane; i < F; i += 32) {
     const int e = list[i];
     const int q = e >> 8, tx = e & 255;
     const int c0 = XOFF - R + tx;
     const int wi = c0 >> 5, sh = c0 & 31;
-    uint32_t alive[K];
+    uint32_t alive[NA];
 #pragma unroll
-    for (int a = 0; a < K; ++a) alive[a] = kMask;
+    for (int a = 0; a < NA; ++a)
+      alive[a] = kPack ? (2 * a + 1 < K ? kMask | (kMask << 16) : kMask) : kMask;
     uint32_t rank = (K * K - 1) / 2, res = 0;
     for (int b = NB - 1; b >= 0; --b) {
       const uint32_t *P = planes + (b * rows + q) * PW + wi;
-      uint32_t seg[K];
+      uint32_t seg[NA];
       uint32_t cnt = 0;
 #pragma unroll
-      for (int a = 0; a < K; ++a) {
-        seg[a] = __funnelshift_r(P[a * PW], P[a * PW + 1], sh);
+      for (int a = 0; a < NA; ++a) {
+        if constexpr (kPack) {
+          const int ra = 2 * a, rb = 2 * a + 1 < K ? 2 * a + 1 : 2 * a;
+          const uint32_t lo = __funnelshift_r(P[ra * PW], P[ra * PW + 1], sh);
+          const uint32_t hi = __funnelshift_r(P[rb * PW], P[rb * PW + 1], sh);
+          seg[a] = __byte_perm(lo, hi, 0x5410);  // bits beyond K in each half meet no live bit
+        } else {
+          seg[a] = __funnelshift_r(P[a * PW], P[a * PW + 1], sh);
+        }
         cnt += __popc(alive[a] & ~seg[a]);
       }
       // keep the 0-bit pixels when the rank falls among them, else the 1-bit ones
@@ -829,7 +868,7 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
       rank -= one ? cnt : 0u;
       res |= (one ? 1u : 0u) << b;
 #pragma unroll
-      for (int a = 0; a < K; ++a) alive[a] &= seg[a] ^ flip;
+      for (int a = 0; a < NA; ++a) alive[a] &= seg[a] ^ flip;
     }
     O[(r0 + q) * TW + tx] = static_cast<T>(res);
   }
@@ -1160,7 +1199,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
           radix_sparse_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {
           uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
-          const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, L.nbmax, lane);
+          uint32_t *pstage = reinterpret_cast<uint32_t *>(wbase + L.w_stage);
+          const uint32_t orv = build_planes_warp<T>(S, planes, pstage, BW, r0, L.plane_rows, L.pw, lane);
           bitplane_strip<T, K>(planes, O, list, flagged, TW, L.plane_rows, L.pw, 32 - __clz(static_cast<int>(orv)),
                                r0, lane);
         }
