@@ -138,8 +138,11 @@ class DeviceGuard {
 static ir_kernel_config default_config(int esize, int k) {
   ir_kernel_config c{};
   c.ctas_per_sm = 0;
-  // measured on GB300 over the 640x512 14-bit sweep (tile sweep of all
-  // strategies): larger tiles amortise the per-tile barriers and bookkeeping
+  // measured on GB300 (tile sweeps of all strategies): the 640x512 14-bit
+  // sweep for k <= 7; for the bit-plane windows, 1280x1024 frames with sparse
+  // random-valued impulses and the mixed batch's dense k = 15 frames, where a
+  // taller strip (16 rows per warp) builds fewer halo rows of planes per
+  // output row
   if (k == 3) {
     c.algo = IR_ALGO_DENSE3;
     c.tile_w = 128;
@@ -150,8 +153,8 @@ static ir_kernel_config default_config(int esize, int k) {
     c.tile_h = 64;
   } else {
     c.algo = IR_ALGO_BITPLANE;
-    c.tile_w = 64;
-    c.tile_h = 64;
+    c.tile_w = 32;
+    c.tile_h = 128;
   }
   (void)esize;
   return c;
