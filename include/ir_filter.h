@@ -169,7 +169,9 @@ ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pitch_bytes, i
                                 void *cuda_stream);
 
 /* Read and clear the handle's device status word (synchronises the device).
- * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call. */
+ * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call;
+ * the handle's tile-order counters are then zeroed as well, since a kernel
+ * that gave up may have left its counter mid-count. */
 ir_status ir_filter_sync_status(ir_filter *h);
 
 /* Border reading for the handle's later calls (single frames, passes, median

@@ -477,7 +477,11 @@ ir_status ir_filter_sync_status(ir_filter *h) {
   unsigned st = 0;
   IR_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost));
   IR_CUDA(h, cudaMemset(h->d_status, 0, sizeof st));
-  if (st & kStatusTimeout) return fail(h, IR_ETIMEOUT, "a bounded device-side wait gave up");
+  if (st & kStatusTimeout) {
+    // a kernel that gave up may not have reset its tile-order slot
+    IR_CUDA(h, cudaMemset(h->d_sched, 0, 2 * sizeof(unsigned) * kSchedSlots));
+    return fail(h, IR_ETIMEOUT, "a bounded device-side wait gave up");
+  }
   return IR_OK;
 }
 
@@ -601,6 +605,20 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     if (descs[i].flagged_count &&
         std::find(counters.begin(), counters.end(), descs[i].flagged_count) == counters.end())
       counters.push_back(descs[i].flagged_count);
+  {
+    // the tile-order slots start every replay at zero (a kernel also resets
+    // its slot when it ends; this covers a replay after one that gave up)
+    cudaMemsetParams mp{};
+    mp.dst = plan->d_sched;
+    mp.elementSize = 4;
+    mp.width = 2 * plan->classes.size();
+    mp.height = 1;
+    mp.pitch = 0;
+    mp.value = 0;
+    cudaGraphNode_t node;
+    IR_CUDA(h, cudaGraphAddMemsetNode(&node, plan->graph, nullptr, 0, &mp));
+    memsets.push_back(node);
+  }
   for (unsigned long long *ctr : counters) {
     cudaMemsetParams mp{};
     mp.dst = ctr;
