@@ -328,6 +328,7 @@ def own_arm(args):
     if rank == 0 and not args.no_quality:
         from paper_1201_3972_gb300 import quality
         result["table1_synthetic"] = quality.table1(flt)
+        result["detail_retention"] = quality.detail_retention(flt)
     if rank == 0 and args.serve_seconds > 0:
         result["serve"] = serve_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline:

@@ -67,11 +67,13 @@ def emittance_to_gray(T: np.ndarray, maxv: int) -> np.ndarray:
 
 
 def add_thin_structures(rng: np.random.Generator, g: np.ndarray, maxv: int,
-                        lines: int = 4, targets: int = 16) -> np.ndarray:
+                        lines: int = 4, targets: int = 16, return_mask: bool = False):
     """Insert 1-pixel hot lines (2 horizontal, 1 vertical, 1 diagonal) and 2x2
-    hot targets at +0.1*maxv over the local field (float, before noise)."""
+    hot targets at +0.1*maxv over the local field (float, before noise).
+    With return_mask, also the boolean mask of the pixels they cover."""
     H, W = g.shape
     g = g.copy()
+    g0 = g.copy()
     bump = 0.1 * maxv
     kinds = ["h", "h", "v", "d"][:lines]
     for kind in kinds:
@@ -91,6 +93,8 @@ def add_thin_structures(rng: np.random.Generator, g: np.ndarray, maxv: int,
         y = int(rng.integers(0, max(H - 1, 1)))
         x = int(rng.integers(0, max(W - 1, 1)))
         g[y:y + 2, x:x + 2] += bump
+    if return_mask:
+        return g, g != g0
     return g
 
 
@@ -114,21 +118,30 @@ def add_impulses(rng: np.random.Generator, img: np.ndarray, p: float, maxv: int,
     return out
 
 
-def make_frame(H: int, W: int, dtype: int, seed: int, sigma: float, p: float,
-               impulse: str = "sp", thin: bool = False) -> np.ndarray:
-    """One seeded synthetic IR frame as a contiguous (H, W) uint8/uint16 array."""
+def make_frame_parts(H: int, W: int, dtype: int, seed: int, sigma: float, p: float,
+                     impulse: str = "sp", thin: bool = False):
+    """The seeded synthetic IR frame with its parts: (frame, the frame before
+    impulses, mask of the thin-structure pixels (all False without them))."""
     if dtype not in MAXV:
         raise ValueError("dtype must be U8, U16 or U14")
     maxv = MAXV[dtype]
     rng = np.random.Generator(np.random.PCG64(seed))
     g = emittance_to_gray(thermal_field(rng, H, W), maxv)
+    mask = np.zeros((H, W), dtype=bool)
     if thin:
-        g = add_thin_structures(rng, g, maxv)
+        g, mask = add_thin_structures(rng, g, maxv, return_mask=True)
     g = g + rng.normal(0.0, sigma, size=(H, W))
     g = np.clip(np.rint(g), 0, maxv).astype(NP_DTYPE[dtype])
+    pre = np.ascontiguousarray(g)
     if p > 0:
         g = add_impulses(rng, g, p, maxv, impulse)
-    return np.ascontiguousarray(g)
+    return np.ascontiguousarray(g), pre, mask
+
+
+def make_frame(H: int, W: int, dtype: int, seed: int, sigma: float, p: float,
+               impulse: str = "sp", thin: bool = False) -> np.ndarray:
+    """One seeded synthetic IR frame as a contiguous (H, W) uint8/uint16 array."""
+    return make_frame_parts(H, W, dtype, seed, sigma, p, impulse, thin)[0]
 
 
 # ---------------------------------------------------------------------------

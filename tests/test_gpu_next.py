@@ -140,3 +140,14 @@ def test_row_bands_on_device(flt, parts):
             rows = download(ob, oa, op, b.h1 - b.h0, W, f.dtype)
             out[b.y0:b.y1] = rows[b.y0 - b.h0:b.y1 - b.h0]
         np.testing.assert_array_equal(out, want)
+
+
+def test_detail_retention_report(flt):
+    """The detail-retention harness runs through the library and reports, per
+    window, the kept fraction and PSNR of thin-structure pixels for FNR and
+    the median filter (a report: the paper's claim is not a gate here)."""
+    res = quality.detail_retention(flt, ks=(3, 5))
+    for k in ("k3", "k5"):
+        for label in ("fnr", "mf"):
+            r = res[k][label]["structure"]
+            assert r["pixels"] > 1000 and 0.0 <= r["kept"] <= 1.0

@@ -411,3 +411,18 @@ def test_pin_harness_accepts_correct_method():
     dict(recursive=True), dict(swap_clamp=True)], ids=str)
 def test_pins_catch_mutation(mutation):
     assert not _pins_pass(lambda a, k: slow_fnr(a, k, **mutation))
+
+
+def test_detail_retention_metric_on_oracle_outputs(oracle_mod):
+    """The retention metric: the unfiltered pre-impulse frame keeps every
+    structure pixel; the oracle's FNR and median filter give fractions in
+    [0, 1]; the structure mask covers the inserted lines and targets."""
+    from paper_1201_3972_gb300 import quality, synth
+    noisy, pre, mask = synth.make_frame_parts(96, 128, synth.U14, 77, 8.0, 0.10, "sp", True)
+    assert 96 * 2 + 96 + 96 <= mask.sum() <= 128 * 2 + 96 * 2 + 16 * 4
+    assert np.array_equal(noisy, synth.make_frame(96, 128, synth.U14, 77, 8.0, 0.10, "sp", True))
+    full = quality.retention(pre, pre, noisy, mask, 16383)
+    assert full["kept"] == 1.0 and full["psnr"] == float("inf") and full["pixels"] > 0
+    for out in (oracle_mod.fnr(noisy, 3)[0], oracle_mod.median_filter(noisy, 3)[0]):
+        r = quality.retention(out, pre, noisy, mask, 16383)
+        assert 0.0 <= r["kept"] <= 1.0
