@@ -138,3 +138,19 @@ def test_native_drive_saturates_served_and_plain(pools_and_ref):
     assert served["frames"] > 1000 and plain["frames"] > 1000
     assert served["mean_batch_frames"] > 1.0
     assert served["p99_ms"] > 0
+
+
+def test_large_windows_served(pools_and_ref):
+    """Streams at k = 9 (pooled network), 15 and 21 (bit planes and the
+    warp-wide radix) through the server: every served output equals the plain
+    path, and the plain path equals the oracle."""
+    import dataclasses
+    streams, pools, _ = pools_and_ref
+    big = [dataclasses.replace(s, k=k, stream_id=i) for i, (s, k) in enumerate(zip(streams[:3], (9, 15, 21)))]
+    ref = serve.reference_hashes(pools, big)
+    for s in big:
+        want, _ = oracle.fnr_mt(pools.frames[s.size_index][0], s.k, 16)
+        assert serve.frame_hash(want) == ref[(s.size_index, 0, s.k)]
+    res = serve.simulate(big, 1.0, pools, ref, verify_every=1, closed_loop=True)
+    assert res["frames_completed"] > 10
+    assert res["mismatches"] == 0 and res["verified"] == res["frames_completed"]
