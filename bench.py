@@ -40,9 +40,9 @@ L2_BYTES = 129 * 10**6
 WORKLOAD = "640x512 14-bit sweep: salt-and-pepper 5/10/20/40%, windows 3/5/7"
 
 
-def recorded_traffic(k: str, frames: int):
-    """DRAM bytes per launch of the class-k kernel from the committed ncu record,
-    or None when the kernel sources changed since that capture."""
+def recorded_profile():
+    """The committed ncu record of the class kernels, or None when the kernel
+    sources changed since that capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic_sweep_640x512_u14.json")
     if not os.path.exists(p):
@@ -53,7 +53,14 @@ def recorded_traffic(k: str, frames: int):
     for src in rec["kernel_sources"]:
         with open(os.path.join(ROOT, src), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != rec["kernel_sources_sha1"] or k not in rec["bytes_per_frame"]:
+    return rec if h.hexdigest() == rec["kernel_sources_sha1"] else None
+
+
+def recorded_traffic(k: str, frames: int):
+    """DRAM bytes per launch of the class-k kernel from the committed ncu record
+    (scaled by the frames of the launch), or None."""
+    rec = recorded_profile()
+    if rec is None or k not in rec["bytes_per_frame"]:
         return None
     return int(rec["bytes_per_frame"][k]) * frames
 
@@ -297,6 +304,9 @@ def own_arm(args):
                 "achieved": round(dom["achieved_gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(dom["achieved_gbs"] / hbm_peak, 4),
                 "traffic": recorded_traffic(dom_k, dom["frames"]),
+                # what does bind it, from the same ncu record (percent of peak)
+                "alu_pipe_pct_ncu": (recorded_profile() or {}).get("alu_pipe_pct", {}).get(dom_k),
+                "issue_active_pct_ncu": (recorded_profile() or {}).get("issue_active_pct", {}).get(dom_k),
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
 
     result = {
