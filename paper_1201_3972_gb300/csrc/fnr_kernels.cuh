@@ -705,13 +705,39 @@ __device__ __forceinline__ void median_pair(const T *S, T *O, int TW, int BW, in
       v[a * K + 2 * R] = __byte_perm(__byte_perm(ua[0], ua[R], sel_a), __byte_perm(ub[0], ub[R], sel_b), 0x7610u);
     }
   } else {
-    const T *ba = S + ya * BW + (XOFF - R) + xa;
-    const T *bb = S + yb * BW + (XOFF - R) + xb;
+    // 8-bit pixels: a window row lies in NWL aligned words; a funnel shift by
+    // the pixel's byte offset realigns them so that window pixel j is byte j,
+    // and one byte permute then puts 257 * a_j and 257 * b_j into the two
+    // 16-bit lanes (v -> 257 v keeps the order, and the low byte of the
+    // selected lane is the 8-bit median)
+    constexpr int NWL = (K + 2) / 4 + 1;  // words covering byte offset (0..3) + K pixels
+    constexpr int NWA = (K + 3) / 4;      // realigned words holding the K pixels
+    const uint32_t *W32 = reinterpret_cast<const uint32_t *>(S);
+    const int BWW = BW >> 2;  // BW is a multiple of 16: rows start on a word
+    const int sa = ya * BW + (XOFF - R) + xa, sb = yb * BW + (XOFF - R) + xb;
+    const uint32_t *wa = W32 + (sa >> 2), *wb = W32 + (sb >> 2);
+    const uint32_t sha = static_cast<uint32_t>(sa & 3) * 8u, shb = static_cast<uint32_t>(sb & 3) * 8u;
 #pragma unroll
-    for (int a = 0; a < K; ++a)
+    for (int a = 0; a < K; ++a) {
+      uint32_t la[NWL + 1], lb[NWL + 1];
 #pragma unroll
-      for (int b = 0; b < K; ++b)
-        v[a * K + b] = __byte_perm(static_cast<uint32_t>(ba[a * BW + b]), static_cast<uint32_t>(bb[a * BW + b]), 0x5410);
+      for (int t = 0; t < NWL; ++t) {
+        la[t] = wa[a * BWW + t];
+        lb[t] = wb[a * BWW + t];
+      }
+      la[NWL] = lb[NWL] = 0u;
+      uint32_t ua[NWA], ub[NWA];
+#pragma unroll
+      for (int t = 0; t < NWA; ++t) {
+        ua[t] = __funnelshift_r(la[t], la[t + 1], sha);
+        ub[t] = __funnelshift_r(lb[t], lb[t + 1], shb);
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const uint32_t q = static_cast<uint32_t>(j & 3);
+        v[a * K + j] = __byte_perm(ua[j >> 2], ub[j >> 2], q | (q << 4) | ((4u + q) << 8) | ((4u + q) << 12));
+      }
+    }
   }
   const uint32_t m = MedianNet<K>::run(v, op);
   O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
