@@ -186,7 +186,7 @@ def own_arm(args):
     d_out = torch.empty_like(d_in)
     base_in, base_out = int(d_in.data_ptr()), int(d_out.data_ptr())
 
-    def descs_for(indices):
+    def descs_for(indices, counter=None):
         arr = (_lib.ir_frame_desc * len(indices))()
         for j, i in enumerate(indices):
             s = specs[i % len(specs)]
@@ -196,7 +196,7 @@ def own_arm(args):
             arr[j].in_pitch = arr[j].out_pitch = W * 2
             arr[j].dtype = _lib.IR_U14
             arr[j].k = s.k
-            arr[j].flagged_count = None
+            arr[j].flagged_count = counter
         return arr
 
     all_idx = list(range(nframes))
@@ -241,11 +241,18 @@ def own_arm(args):
         ms = statistics.median(durs)
         px = len(idx) * fpx
         algo_bytes = px * 2 * 2  # read + write, 2 bytes per pixel
+        sub.close()
+        # the flagged fraction of the class (one counted run, untimed)
+        ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+        counted = _lib.BatchPlan(flt, descs_for(idx, int(ctr.data_ptr())))
+        counted.launch(stream)
+        torch.cuda.synchronize()
+        counted.close()
         per_k[str(k)] = {"mpx_s": px / (ms * 1e-3) / 1e6, "ms": ms, "frames": len(idx),
                          "achieved_gbs": algo_bytes / (ms * 1e-3) / 1e9,
                          "hbm_frac": algo_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                         "flagged_fraction": int(ctr.item()) / px,
                          "config": flt.get_config(_lib.IR_U14, k)}
-        sub.close()
     clk = clocks.stop()
 
     # plain per-frame path on the same frames (one ir_filter_run2 per frame)

@@ -320,6 +320,42 @@ class Filter:
         c = ir_kernel_config(tile_w, tile_h, algo, ctas_per_sm)
         _check(self.lib, self.h, self.lib.ir_filter_set_config(self.h, dtype, k, ctypes.byref(c)))
 
+    # -- tuning table on disk -----------------------------------------------------
+    def configs(self) -> dict:
+        """The handle's (strategy, tile) table: {"<dtype>:<k>": config} for 8- and 16-bit pixels."""
+        return {f"{dt}:{k}": self.get_config(dt, k) for dt in (IR_U8, IR_U16) for k in range(3, 22, 2)}
+
+    def save_configs(self, path: str, device_name: str) -> None:
+        """Store the table under ``device_name`` in a JSON file (other devices' tables are kept), e.g.
+        after ``autotune`` runs, so that later processes on the same GPU model can reuse it."""
+        import json
+        import os
+        table = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                table = json.load(fh)
+        table[device_name] = self.configs()
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+    def load_configs(self, path: str, device_name: str) -> bool:
+        """Apply the table stored under ``device_name``; False when the file or the entry is missing.
+        An entry the library rejects raises IrError."""
+        import json
+        import os
+        if not os.path.exists(path):
+            return False
+        with open(path) as fh:
+            table = json.load(fh).get(device_name)
+        if table is None:
+            return False
+        for key, c in table.items():
+            dt, k = (int(v) for v in key.split(":"))
+            self.set_config(dt, k, c["tile_w"], c["tile_h"], c["algo"], c.get("ctas_per_sm", 0))
+        return True
+
 
 class BatchPlan:
     """An uploaded descriptor set with its captured graph (``ir_batch_plan``)."""

@@ -4,11 +4,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fnr_params.h"
 #include "ir_filter.h"
 
 namespace fnr {
+
+// An NVTX range for the lifetime of the object: the library's calls show up
+// by name on a profiler's timeline (a no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct ClassLaunch {
   int esize = 0, k = 0;

@@ -404,6 +404,7 @@ void ir_filter_destroy(ir_filter *h) {
 
 ir_status ir_filter_run2(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H, int W,
                          ir_dtype dtype, int k, void *cuda_stream, unsigned long long *flagged_count) {
+  fnr::NvtxRange nvtx_range("ir_filter_run2");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
   if (s != IR_OK) return s;
@@ -414,6 +415,7 @@ ir_status ir_filter_run2(ir_filter *h, const void *in, size_t in_pitch, void *ou
 
 ir_status ir_filter_run(ir_filter *h, void *frame, int H, int W, size_t pitch_bytes, ir_dtype dtype, int k,
                         void *cuda_stream) {
+  fnr::NvtxRange nvtx_range("ir_filter_run");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (!frame) return fail(h, IR_EINVAL, "null frame pointer");
   if (H < 1 || W < 1 || !valid_dtype(dtype)) return check_frame(h, frame, pitch_bytes, frame, pitch_bytes, H, W, dtype, k);
@@ -432,6 +434,7 @@ ir_status ir_filter_run(ir_filter *h, void *frame, int H, int W, size_t pitch_by
 
 ir_status ir_filter_median_filter(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H,
                                   int W, ir_dtype dtype, int k, void *cuda_stream, unsigned long long *median_count) {
+  fnr::NvtxRange nvtx_range("ir_filter_median_filter");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
   if (s != IR_OK) return s;
@@ -443,6 +446,7 @@ ir_status ir_filter_median_filter(ir_filter *h, const void *in, size_t in_pitch,
 ir_status ir_filter_run_passes(ir_filter *h, const void *in, size_t in_pitch, void *out, size_t out_pitch, int H,
                                int W, ir_dtype dtype, int k, int passes, void *cuda_stream,
                                unsigned long long *flagged_per_pass) {
+  fnr::NvtxRange nvtx_range("ir_filter_run_passes");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (passes < 1 || passes > 64) return fail(h, IR_EINVAL, "passes must be in [1, 64] (got %d)", passes);
   ir_status s = check_frame(h, in, in_pitch, out, out_pitch, H, W, dtype, k);
@@ -532,6 +536,7 @@ ir_status ir_filter_set_config(ir_filter *h, ir_dtype dtype, int k, const ir_ker
 // batch plans
 // ---------------------------------------------------------------------------
 ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, ir_batch_plan **out) {
+  fnr::NvtxRange nvtx_range("ir_batch_plan_create");
   if (!h || !out) return fail(h, IR_EINVAL, "null argument");
   *out = nullptr;
   if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
@@ -650,6 +655,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
 }
 
 ir_status ir_batch_plan_launch(ir_batch_plan *plan, void *cuda_stream) {
+  fnr::NvtxRange nvtx_range("ir_batch_plan_launch");
   if (!plan) return fail(nullptr, IR_EINVAL, "null plan");
   DeviceGuard g(plan->h->device);
   IR_CUDA(plan->h, cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(cuda_stream)));
@@ -671,6 +677,7 @@ void ir_batch_plan_destroy(ir_batch_plan *plan) {
 }
 
 ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, void *cuda_stream) {
+  fnr::NvtxRange nvtx_range("ir_filter_run_batch");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
   PlanKey key;
@@ -751,6 +758,7 @@ static void tuning_frame(std::vector<unsigned char> &buf, int H, int W, int esiz
 }
 
 ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, void *cuda_stream) {
+  fnr::NvtxRange nvtx_range("ir_filter_autotune");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (!valid_dtype(dtype) || !valid_k(k) || H < 1 || W < 1) return fail(h, IR_EINVAL, "bad tuning arguments");
   DeviceGuard g(h->device);

@@ -130,6 +130,7 @@ ir_status make_lane(ir_server *s, Lane &L) {
 // Launch one batch on lane L (batcher thread, no lock held): reads only the
 // lane's own snapshot.
 ir_status launch_batch(ir_server *s, Lane &L) {
+  NvtxRange nvtx_range("ir_server batch");
   ir_filter *h = s->h;
   const int n = static_cast<int>(L.jobs.size());
   for (const Job &j : L.jobs) {

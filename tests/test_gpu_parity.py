@@ -268,3 +268,24 @@ def test_launch_counter_counts_kernels(flt):
     for _ in range(3):
         gpu_fnr(flt, f, 3, count=False)
     assert flt.launch_count() - before == 3
+
+
+def test_tuning_table_round_trip(flt, tmp_path):
+    """A tuned table saved under a device name and loaded into a fresh handle
+    gives the same configurations, and results stay exact with it."""
+    import torch
+    name = torch.cuda.get_device_name(0)
+    flt.set_config(_lib.IR_U16, 7, 128, 32, _lib.IR_ALGO_NETWORK)
+    path = str(tmp_path / "tuning.json")
+    flt.save_configs(path, name)
+    other = _lib.Filter(0)
+    try:
+        assert other.configs() != flt.configs()
+        assert other.load_configs(path, name)
+        assert other.configs() == flt.configs()
+        assert not other.load_configs(path, name + " (another model)")
+        a = np.random.default_rng(3).integers(0, 65536, (70, 150)).astype(np.uint16)
+        check(other, a, 7)
+    finally:
+        other.close()
+        flt.set_config(_lib.IR_U16, 7, 0, 0, _lib.IR_ALGO_AUTO)
