@@ -255,6 +255,31 @@ def own_arm(args):
                          "config": flt.get_config(_lib.IR_U14, k)}
     clk = clocks.stop()
 
+    # the directional detector (Fig. 1) on the same window classes: throughput
+    # and flagged fraction (its parity with the oracle is in the test suite)
+    directional = {}
+    if rank == 0 and not args.no_directional:
+        flt.set_detector("directional")
+        try:
+            for k in (3, 5, 7):
+                idx = [i for i in all_idx if specs[i % len(specs)].k == k]
+                sub = _lib.BatchPlan(flt, descs_for(idx))
+                for _ in range(args.warmup):
+                    sub.launch(stream)
+                ms = statistics.median(time_events(torch, lambda: sub.launch(stream), max(args.steps, 5), stream))
+                sub.close()
+                ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+                counted = _lib.BatchPlan(flt, descs_for(idx, int(ctr.data_ptr())))
+                counted.launch(stream)
+                torch.cuda.synchronize()
+                counted.close()
+                px = len(idx) * fpx
+                directional[str(k)] = {"mpx_s": round(px / (ms * 1e-3) / 1e6, 1), "ms": round(ms, 4),
+                                       "flagged_fraction": round(int(ctr.item()) / px, 4),
+                                       "extreme_detector_mpx_s": round(per_k[str(k)]["mpx_s"], 1)}
+        finally:
+            flt.set_detector("extreme")
+
     # plain per-frame path on the same frames (one ir_filter_run2 per frame)
     def plain_step():
         for i in all_idx:
@@ -336,6 +361,8 @@ def own_arm(args):
         "gpu_launches": int(gpu_launches), "launches_per_step": launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
     }
+    if directional:
+        result["directional_detector"] = directional
     if rank == 0:
         result["single_frame"] = single_frame_leg(flt, stream, args)
     if rank == 0 and not args.no_batch_leg:
@@ -557,6 +584,7 @@ def main():
     ap.add_argument("--no-batch-leg", action="store_true", help="skip the 256-frame mixed batch")
     ap.add_argument("--no-large-k", action="store_true", help="skip the k = 9..21 windows on 1280x1024 frames")
     ap.add_argument("--no-quality", action="store_true", help="skip the Table 1 style PSNR comparison")
+    ap.add_argument("--no-directional", action="store_true", help="skip the directional-detector leg")
     ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:

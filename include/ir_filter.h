@@ -71,6 +71,15 @@ typedef enum {
   IR_BORDER_ZERO = 2         /* outside pixels read as 0 */
 } ir_border;
 
+/* Which pixels are noisy (Sec. 3.3). Both replace a noisy pixel by the median
+ * of its k x k window (Sec. 3.4) and leave every other pixel bit-identical. */
+typedef enum {
+  IR_DETECT_EXTREME = 0,     /* Eq. 3a/3b: g(x, y) equals the window's min or max (default) */
+  IR_DETECT_DIRECTIONAL = 1  /* Fig. 1: along none of the four lines through p(x, y) (horizontal,
+                                vertical, two diagonals) does g(x, y) lie strictly between its two
+                                neighbours at distance one; the lines read the border like the window */
+} ir_detector;
+
 /* Kernel configuration for one (dtype, k) class. tile_w, tile_h: output tile
  * in pixels (multiples of 8; tile_w + halo <= 256 pixels). ctas_per_sm: 0 = as
  * many as fit. */
@@ -179,6 +188,15 @@ ir_status ir_filter_sync_status(ir_filter *h);
  * ir_filter_run_noalloc and the server always replicate. */
 ir_status ir_filter_set_border(ir_filter *h, ir_border mode);
 ir_border ir_filter_get_border(const ir_filter *h);
+
+/* Noise detector for the handle's later calls, like ir_filter_set_border
+ * (single frames, in place, passes, batch plans created afterwards; tuning
+ * times the detector in use). flagged_count counts the pixels the detector
+ * flags. The median filter flags every pixel whatever the detector.
+ * IR_EINVAL for an unknown detector. ir_filter_run_noalloc and the server
+ * always use IR_DETECT_EXTREME. */
+ir_status ir_filter_set_detector(ir_filter *h, ir_detector detector);
+ir_detector ir_filter_get_detector(const ir_filter *h);
 
 /* Tuning. ir_filter_autotune times every built candidate for (dtype, k) on a
  * synthetic H x W frame on `cuda_stream` and keeps the fastest; the table is

@@ -51,6 +51,8 @@ def _load():
         lib.oracle_fnr_stack.restype = ll
         lib.oracle_fnr_border.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32, i32]
         lib.oracle_fnr_border.restype = ll
+        lib.oracle_fnr_directional.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32, i32]
+        lib.oracle_fnr_directional.restype = ll
         lib.oracle_median_filter.argtypes = [vp, ll, vp, ll, i32, i32, i32, i32]
         lib.oracle_median_filter.restype = ll
         lib.oracle_introsort.argtypes = [vp, ctypes.c_long, i32]
@@ -94,6 +96,22 @@ def fnr_border(frame: np.ndarray, k: int, border: str):
     H, W = frame.shape
     f = lib.oracle_fnr_border(frame.ctypes.data, frame.strides[0], out.ctypes.data, out.strides[0],
                               H, W, es, int(k), BORDERS[border])
+    if f < 0:
+        raise ValueError("oracle rejected arguments")
+    return out, int(f)
+
+
+def fnr_directional(frame: np.ndarray, k: int, border: str = "replicate"):
+    """FNR with the directional detector (Fig. 1): a pixel is noisy iff along
+    none of the four lines through it (horizontal, vertical, two diagonals)
+    it lies strictly between its two neighbours; noisy pixels take the k x k
+    window median. Returns (filtered frame, flagged count)."""
+    lib = _load()
+    es = _check_frame(frame)
+    out = np.empty(frame.shape, dtype=frame.dtype)
+    H, W = frame.shape
+    f = lib.oracle_fnr_directional(frame.ctypes.data, frame.strides[0], out.ctypes.data, out.strides[0],
+                                   H, W, es, int(k), BORDERS[border])
     if f < 0:
         raise ValueError("oracle rejected arguments")
     return out, int(f)

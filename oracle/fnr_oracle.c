@@ -296,6 +296,61 @@ long long oracle_median_filter(const void *in, long long in_pitch, void *out, lo
     return (long long)H * W;
 }
 
+/* The directional detector, an option beside Eq. 3a/3b. Fig. 1 (its image
+ * is missing) compares the centre of a 3x3 window with its two neighbours
+ * along each direction, and Sec. 3 rests on the gray level of a signal pixel
+ * varying monotonically over an object's surface (Eq. 1 and 2). Reading:
+ * p(x, y) is a signal pixel iff along at least one of the four lines through
+ * it (horizontal, vertical, the two diagonals) g(x, y) lies strictly between
+ * its two neighbours at distance one; otherwise it is noisy and takes the
+ * median of the k x k window S_xy (Sec. 3.4). Neighbours and window are read
+ * under the same border reading. Returns the number of noisy pixels, or -1
+ * for bad arguments. */
+long long oracle_fnr_directional(const void *in, long long in_pitch, void *out, long long out_pitch,
+                                 int H, int W, int esize, int k, int border)
+{
+    if (!args_ok(in, in_pitch, out, out_pitch, H, W, esize, k) || border < 0 || border > 2) return -1;
+    /* one end of each line; the other end is the opposite offset */
+    static const int line_dy[4] = {0, -1, -1, -1};
+    static const int line_dx[4] = {-1, 0, -1, 1};
+    const unsigned char *src = (const unsigned char *)in;
+    const int r = (k - 1) / 2;
+    const int n = k * k;
+    uint32_t *w = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!w) return -1;
+    long long flagged = 0;
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint32_t g = load_px(src, in_pitch, esize, y, x);
+            int monotone = 0;
+            for (int d = 0; d < 4; d++) {
+                int ya = border_index(y + line_dy[d], H, border), xa = border_index(x + line_dx[d], W, border);
+                int yb = border_index(y - line_dy[d], H, border), xb = border_index(x - line_dx[d], W, border);
+                uint32_t a = (ya < 0 || xa < 0) ? 0u : load_px(src, in_pitch, esize, ya, xa);
+                uint32_t b = (yb < 0 || xb < 0) ? 0u : load_px(src, in_pitch, esize, yb, xb);
+                if ((a < g && g < b) || (b < g && g < a)) monotone = 1;
+            }
+            uint32_t v = g;
+            if (!monotone) {
+                int i = 0;
+                for (int dy = -r; dy <= r; dy++) {
+                    int yy = border_index(y + dy, H, border);
+                    for (int dx = -r; dx <= r; dx++) {
+                        int xx = border_index(x + dx, W, border);
+                        w[i++] = (yy < 0 || xx < 0) ? 0u : load_px(src, in_pitch, esize, yy, xx);
+                    }
+                }
+                oracle_introsort(w, n, -1);
+                v = w[(n - 1) / 2];
+                flagged++;
+            }
+            store_px((unsigned char *)out, out_pitch, esize, y, x, v);
+        }
+    }
+    free(w);
+    return flagged;
+}
+
 /* Same result, rows split into contiguous bands over `threads` POSIX threads
  * (used only to time the oracle on all host cores). */
 typedef struct {

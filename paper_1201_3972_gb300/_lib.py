@@ -21,6 +21,8 @@ IR_U8, IR_U16, IR_U14 = 0, 1, 2
 IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE = 0, 1, 2, 3
 IR_BORDER_REPLICATE, IR_BORDER_MIRROR, IR_BORDER_ZERO = 0, 1, 2
 BORDER_CODES = {"replicate": IR_BORDER_REPLICATE, "mirror": IR_BORDER_MIRROR, "zero": IR_BORDER_ZERO}
+IR_DETECT_EXTREME, IR_DETECT_DIRECTIONAL = 0, 1
+DETECTOR_CODES = {"extreme": IR_DETECT_EXTREME, "directional": IR_DETECT_DIRECTIONAL}
 ALGO_NAMES = {IR_ALGO_AUTO: "auto", IR_ALGO_DENSE3: "dense3", IR_ALGO_NETWORK: "network",
               IR_ALGO_BITPLANE: "bitplane"}
 
@@ -30,7 +32,7 @@ EXPORTED = (
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
     "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
-    "ir_filter_get_border",
+    "ir_filter_get_border", "ir_filter_set_detector", "ir_filter_get_detector",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
     "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
@@ -118,6 +120,8 @@ def load(path: Optional[str] = None):
             "ir_filter_median_filter": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
             "ir_filter_set_border": ([vp, i32], i32),
             "ir_filter_get_border": ([vp], i32),
+            "ir_filter_set_detector": ([vp, i32], i32),
+            "ir_filter_get_detector": ([vp], i32),
             "ir_filter_run_passes": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, i32, vp, vp], i32),
             "ir_server_create": ([i32, ctypes.POINTER(ir_server_config), ctypes.POINTER(vp)], i32),
             "ir_server_destroy": ([vp], None),
@@ -243,6 +247,15 @@ class Filter:
 
     def get_border(self) -> int:
         return int(self.lib.ir_filter_get_border(self.h))
+
+    def set_detector(self, detector) -> None:
+        """Noise detector for later calls: "extreme" (Eq. 3a/3b, default) or
+        "directional" (Fig. 1)."""
+        code = DETECTOR_CODES[detector] if isinstance(detector, str) else int(detector)
+        _check(self.lib, self.h, self.lib.ir_filter_set_detector(self.h, code))
+
+    def get_detector(self) -> int:
+        return int(self.lib.ir_filter_get_detector(self.h))
 
     def median_filter(self, src, dst, k: int, u14: bool = False, stream=None, median_count=None) -> None:
         """Standard median filter (every pixel), the paper's MF baseline."""

@@ -346,12 +346,36 @@ __device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
 // (hi lane of a, lo lane of b): the odd-aligned pair between two even pairs.
 __device__ __forceinline__ uint32_t odd_pair(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x5432); }
 
+// The directional detector (Fig. 1) on the two pixels of word j + 1 of row b,
+// where a, b, c are three consecutive rows of pixel pairs as load_row8 gives
+// them (word q: the pixels 2q - 2 and 2q - 1 from the first centre column).
+// Per 16-bit lane: 1 where the pixel lies strictly between its two
+// neighbours along at least one of the four lines through it (a signal
+// pixel: its gray level varies monotonically there, Sec. 3), 0 where along
+// none (noisy).
+__device__ __forceinline__ uint32_t strictly_between(uint32_t g, uint32_t u, uint32_t v, const PackedOp op) {
+  const uint32_t lo = vmin2(u, v), hi = vmax2(u, v);
+  // max(g, lo) - lo is nonzero iff g > lo, hi - min(g, hi) iff g < hi; both
+  // differences are lane-wise non-negative, so no borrow crosses lanes
+  return vmin2(vmin2(op.sub(vmax2(g, lo), lo), op.sub(hi, vmin2(g, hi))), 0x00010001u);
+}
+
+__device__ __forceinline__ uint32_t directional_sig(const uint32_t (&a)[6], const uint32_t (&b)[6],
+                                                    const uint32_t (&c)[6], int j, const PackedOp op) {
+  const uint32_t g = b[j + 1];
+  uint32_t sig = strictly_between(g, odd_pair(b[j], b[j + 1]), odd_pair(b[j + 1], b[j + 2]), op);  // west, east
+  sig |= strictly_between(g, a[j + 1], c[j + 1], op);                                            // north, south
+  sig |= strictly_between(g, odd_pair(a[j], a[j + 1]), odd_pair(c[j + 1], c[j + 2]), op);        // north-west, south-east
+  sig |= strictly_between(g, odd_pair(a[j + 1], a[j + 2]), odd_pair(c[j], c[j + 1]), op);        // north-east, south-west
+  return sig;
+}
+
 // Output rows [r0, r0+SR) of the tile, written straight to the frame: 16-byte
 // (u16) or 8-byte (u8) stores when the 8 pixels are inside the frame and the
 // frame is 16-byte aligned, else per-pixel stores clipped to the frame.
 // tw_valid, th_valid: the part of the tile inside the frame. tile_w / 8 is a
 // power of two (seg_shift = log2 of it).
-template <typename T, bool COUNT, bool ALL>
+template <typename T, bool COUNT, int MODE>
 __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int TW, int BW, int r0, int SR,
                              int seg_shift, int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged,
                              const PackedOp op) {
@@ -366,6 +390,15 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
     uint32_t e[4][6];
 #pragma unroll
     for (int rr = 0; rr < 4; ++rr) load_row8<T>(S + (ty + rr) * BW + XOFF + tx, e[rr]);
+    // directional detector: the flags of both output rows first, as bit
+    // 4 o + pp of each 16-bit lane, so that the rows need not stay live
+    uint32_t dsig = 0;
+    if constexpr (MODE == kModeDirectional) {
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) dsig |= directional_sig(e[o], e[o + 1], e[o + 2], pp, op) << (4 * o + pp);
+    }
     uint32_t lo[2][6], md[2][6], hi[2][6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
@@ -400,11 +433,18 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
         const uint32_t c = e[1 + o][pp + 1];
         // per 16-bit lane: 1 where g_min < c < g_max (signal pixel), 0 where c
         // equals g_min or g_max (noisy); c - g_min and g_max - c never borrow
-        // across lanes since g_min <= c <= g_max. ALL: standard median filter
-        const uint32_t sig = ALL ? 0u : vmin2(vmin2(op.sub(c, gmin), op.sub(gmax, c)), 0x00010001u);
+        // across lanes since g_min <= c <= g_max. The standard median filter
+        // treats every pixel as noisy; the directional detector tests lines.
+        uint32_t sig;
+        if constexpr (MODE == kModeMedian)
+          sig = 0u;
+        else if constexpr (MODE == kModeDirectional)
+          sig = (dsig >> (4 * o + pp)) & 0x00010001u;
+        else
+          sig = vmin2(vmin2(op.sub(c, gmin), op.sub(gmax, c)), 0x00010001u);
         const uint32_t keep = sig * 0xffffu;
         res[pp] = (c & keep) | (gm & ~keep);
-        if constexpr (COUNT) {
+        if constexpr (COUNT && MODE != kModeDirectional) {
           const int col = tx + 2 * pp;
           const uint32_t valid =
               (ty + o < th_valid) ? ((col < tw_valid ? 1u : 0u) | (col + 1 < tw_valid ? 0x10000u : 0u)) : 0u;
@@ -421,6 +461,13 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
             if (tx + q < tw_valid) dst[q] = static_cast<T>((res[q >> 1] >> (16 * (q & 1))) & 0xffffu);
         }
       }
+    }
+    if constexpr (COUNT && MODE == kModeDirectional) {
+      // in-frame pixels, in the bit order of dsig
+      const int nlo = min(max((tw_valid - tx + 1) >> 1, 0), 4), nhi = min(max((tw_valid - tx) >> 1, 0), 4);
+      const uint32_t row = ((1u << nlo) - 1u) | (((1u << nhi) - 1u) << 16);
+      const uint32_t valid = (ty < th_valid ? row : 0u) | (ty + 1 < th_valid ? row << 4 : 0u);
+      flagged += __popc(~dsig & valid);
     }
   }
 }
@@ -580,7 +627,7 @@ __device__ __forceinline__ void store_centre8<uint8_t>(uint8_t *p, const uint32_
 
 template <typename T, int K>
 __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_t *vmaxP, T *O, uint16_t *list, int TW,
-                                int BW, int NPS, int r0, int SR, int tw_valid, int th_valid, bool all,
+                                int BW, int NPS, int r0, int SR, int tw_valid, int th_valid, int mode,
                                 const FastDiv &divG, const PackedOp op, int lane) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
@@ -601,48 +648,59 @@ __device__ int horizontal_pairs(const T *S, const uint32_t *vminP, const uint32_
       q = static_cast<int>(divG.div(static_cast<uint32_t>(it)));
       const int grp = it - q * gpr;
       x0p = grp * 2 * PPI;                 // first output column of the item (tile coordinates)
-      uint32_t mnw[4 * NV], mxw[4 * NV];
-      const uint4 *vn = reinterpret_cast<const uint4 *>(vminP + q * NPS + (x0p >> 1));
-      const uint4 *vx = reinterpret_cast<const uint4 *>(vmaxP + q * NPS + (x0p >> 1));
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-        const uint4 a = vn[i], b = vx[i];
-        mnw[4 * i] = a.x; mnw[4 * i + 1] = a.y; mnw[4 * i + 2] = a.z; mnw[4 * i + 3] = a.w;
-        mxw[4 * i] = b.x; mxw[4 * i + 1] = b.y; mxw[4 * i + 2] = b.z; mxw[4 * i + 3] = b.w;
-      }
       const int ty = r0 + q;
       uint32_t c[PPI];
       load_centre8<T>(S + (ty + R) * BW + XOFF + x0p, c);
       store_centre8<T>(O + ty * TW + x0p, c);
       uint32_t sig = 0;                    // per 16-bit lane, bit j: pair j is a signal pixel
+      if (mode == kModeDirectional) {
+        // the rows above, through and below the centres
+        uint32_t ra[6], rb[6], rc[6];
+        const T *sp = S + (ty + R - 1) * BW + XOFF + x0p;
+        load_row8<T>(sp, ra);
+        load_row8<T>(sp + BW, rb);
+        load_row8<T>(sp + 2 * BW, rc);
 #pragma unroll
-      for (int j = 0; j < PPI; ++j) {
-        uint32_t gmin = 0xffffffffu, gmax = 0u;
+        for (int j = 0; j < PPI; ++j) sig = imad(directional_sig(ra, rb, rc, j, op), op.unit << j, sig);
+      } else {
+        uint32_t mnw[4 * NV], mxw[4 * NV];
+        const uint4 *vn = reinterpret_cast<const uint4 *>(vminP + q * NPS + (x0p >> 1));
+        const uint4 *vx = reinterpret_cast<const uint4 *>(vmaxP + q * NPS + (x0p >> 1));
 #pragma unroll
-        for (int d = -R; d <= R; ++d) {
-          const int col = OFF0 + 2 * j + d;  // relative to x0p, plus OFF0 (compile time)
-          const int w = col >> 1;
-          uint32_t a, b;
-          if (col & 1) {
-            a = __byte_perm(mnw[w], mnw[w + 1], 0x5432);
-            b = __byte_perm(mxw[w], mxw[w + 1], 0x5432);
-          } else {
-            a = mnw[w];
-            b = mxw[w];
-          }
-          gmin = d == -R ? a : vmin2(gmin, a);
-          gmax = d == -R ? b : vmax2(gmax, b);
+        for (int i = 0; i < NV; ++i) {
+          const uint4 a = vn[i], b = vx[i];
+          mnw[4 * i] = a.x; mnw[4 * i + 1] = a.y; mnw[4 * i + 2] = a.z; mnw[4 * i + 3] = a.w;
+          mxw[4 * i] = b.x; mxw[4 * i + 1] = b.y; mxw[4 * i + 2] = b.z; mxw[4 * i + 3] = b.w;
         }
-        // 1 per 16-bit lane where g_min < c < g_max, 0 where c is an extreme
-        // (no borrow between lanes: g_min <= c <= g_max lane-wise)
-        const uint32_t z = vmin2(vmin2(op.sub(c[j], gmin), op.sub(gmax, c[j])), 0x00010001u);
-        sig = imad(z, op.unit << j, sig);
+#pragma unroll
+        for (int j = 0; j < PPI; ++j) {
+          uint32_t gmin = 0xffffffffu, gmax = 0u;
+#pragma unroll
+          for (int d = -R; d <= R; ++d) {
+            const int col = OFF0 + 2 * j + d;  // relative to x0p, plus OFF0 (compile time)
+            const int w = col >> 1;
+            uint32_t a, b;
+            if (col & 1) {
+              a = __byte_perm(mnw[w], mnw[w + 1], 0x5432);
+              b = __byte_perm(mxw[w], mxw[w + 1], 0x5432);
+            } else {
+              a = mnw[w];
+              b = mxw[w];
+            }
+            gmin = d == -R ? a : vmin2(gmin, a);
+            gmax = d == -R ? b : vmax2(gmax, b);
+          }
+          // 1 per 16-bit lane where g_min < c < g_max, 0 where c is an extreme
+          // (no borrow between lanes: g_min <= c <= g_max lane-wise)
+          const uint32_t z = vmin2(vmin2(op.sub(c[j], gmin), op.sub(gmax, c[j])), 0x00010001u);
+          sig = imad(z, op.unit << j, sig);
+        }
       }
       // in-frame pixels of the item, in the bit order of fm
       const int n = ty < th_valid ? min(max(tw_valid - x0p, 0), 2 * PPI) : 0;
       const uint32_t valid = ((1u << ((n + 1) >> 1)) - 1u) | (((1u << (n >> 1)) - 1u) << 4);
       const uint32_t noisy = ~sig & 0x000f000fu;
-      fm = (all ? 0xffu : ((noisy & 0xfu) | (noisy >> 12))) & valid;
+      fm = (mode == kModeMedian ? 0xffu : ((noisy & 0xfu) | (noisy >> 12))) & valid;
     }
     const int cnt = __popc(fm);
     int incl = cnt;
@@ -1140,20 +1198,25 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
       if (p.mode == kModeMedian) {
-        dense3_strip<T, false, true>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                                     flagged, d3op);
+        dense3_strip<T, false, kModeMedian>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
+                                            lane, flagged, d3op);
         if (cur.counted && lane == 0) {  // every in-frame pixel of the strip takes a median
           const int rows = min(SR, cur.H - y0 - r0), cols = min(TW, cur.W - x0);
           atomicAdd(cf->flagged, static_cast<unsigned long long>(rows) * static_cast<unsigned long long>(cols));
         }
+      } else if (p.mode == kModeDirectional) {
+        dense3_strip<T, true, kModeDirectional>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0,
+                                                vec_ok, lane, flagged, d3op);
+        flagged = __reduce_add_sync(0xffffffffu, flagged);
+        if (cur.counted && lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else if (cur.counted) {
-        dense3_strip<T, true, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                                     flagged, d3op);
+        dense3_strip<T, true, kModeFnr>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
+                                        lane, flagged, d3op);
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if (lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else {
-        dense3_strip<T, false, false>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
-                                      lane, flagged, d3op);
+        dense3_strip<T, false, kModeFnr>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
+                                         lane, flagged, d3op);
       }
     } else if constexpr (ALGO == ALGO_NETWORK && PoolMedians<K>::value) {
       // Every consumer warp takes part, live strip or not: the strips' flagged
@@ -1176,10 +1239,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       if (live) {
         uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
         uint32_t *vmax = reinterpret_cast<uint32_t *>(wbase + L.w_vmax);
-        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
+        // the window extremes (the directional detector needs none)
+        if (p.mode != kModeDirectional) vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
         __syncwarp();
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
-                                         p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
+                                         p.mode, divG, PackedOp{p.unit, 0u - p.unit}, lane);
       }
       if (lane == 0) {
         counts[s * kConsumerWarps + warp] = flagged;
@@ -1215,10 +1279,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         uint16_t *list = reinterpret_cast<uint16_t *>(wbase + L.w_list);
         uint32_t *vmin = reinterpret_cast<uint32_t *>(wbase + L.w_vmin);
         uint32_t *vmax = reinterpret_cast<uint32_t *>(wbase + L.w_vmax);
-        vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
+        // the window extremes (the directional detector needs none)
+        if (p.mode != kModeDirectional) vertical_pairs<T, K>(S, vmin, vmax, BW, L.np, L.nps, L.cb, r0, SR, divNP, lane);
         __syncwarp();
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
-                                         p.mode == kModeMedian, divG, PackedOp{p.unit, 0u - p.unit}, lane);
+                                         p.mode, divG, PackedOp{p.unit, 0u - p.unit}, lane);
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane, PackedOp{p.unit, 0u - p.unit});
         } else if (flagged <= SparseLimit<K>::value) {

@@ -47,7 +47,7 @@ struct alignas(128) FnrParams {
   // indices, sched[1] counts CTAs that are done; the last CTA zeroes both, so
   // a slot is ready for the next launch ordered after this one
   unsigned int *sched;
-  int mode;                        // kModeFnr, or kModeMedian: every pixel is treated as noisy
+  int mode;                        // kModeFnr, kModeMedian or kModeDirectional: which pixels are noisy
   int border;                      // kBorderReplicate / kBorderMirror / kBorderZero
   unsigned int unit = 1u;          // always 1: multiplier of the median networks' multiply-add form
 };
@@ -58,6 +58,10 @@ constexpr int kBorderZero = 2;       // outside pixels read 0
 
 constexpr int kModeFnr = 0;        // replace only pixels equal to a window extreme (Sec. 3.3-3.4)
 constexpr int kModeMedian = 1;     // standard median filter: replace every pixel (the paper's MF, Sec. 2)
+// directional detector (Fig. 1): a pixel is noisy iff along none of the four
+// lines through it (horizontal, vertical, two diagonals) it lies strictly
+// between its two neighbours; noisy pixels take the k x k median as in FNR
+constexpr int kModeDirectional = 2;
 
 constexpr unsigned int kStatusTimeout = 1u;
 

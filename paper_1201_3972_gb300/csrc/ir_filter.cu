@@ -70,6 +70,7 @@ struct ir_filter {
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   ir_kernel_config cfg[2][kNumK];
   int border = kBorderReplicate;
+  int detector = kModeFnr;  // kModeFnr (Eq. 3a/3b) or kModeDirectional
   std::string last_error;
   std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, smem) -> CTAs per SM
   std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
@@ -324,7 +325,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   cl.prm.tile_h = cl.cfg.tile_h;
   cl.prm.status = h->d_status;
   cl.prm.launches = h->d_launches;
-  cl.prm.mode = mode;
+  cl.prm.mode = mode == kModeFnr ? h->detector : mode;
   cl.prm.border = h->border;
   ir_status s = host_prepare_class(h, cl);
   if (s != IR_OK) return s;
@@ -512,6 +513,18 @@ ir_border ir_filter_get_border(const ir_filter *h) {
   return h ? static_cast<ir_border>(h->border) : IR_BORDER_REPLICATE;
 }
 
+ir_status ir_filter_set_detector(ir_filter *h, ir_detector detector) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (detector != IR_DETECT_EXTREME && detector != IR_DETECT_DIRECTIONAL)
+    return fail(h, IR_EINVAL, "unknown detector %d", static_cast<int>(detector));
+  h->detector = detector == IR_DETECT_DIRECTIONAL ? kModeDirectional : kModeFnr;
+  return IR_OK;
+}
+
+ir_detector ir_filter_get_detector(const ir_filter *h) {
+  return h && h->detector == kModeDirectional ? IR_DETECT_DIRECTIONAL : IR_DETECT_EXTREME;
+}
+
 ir_status ir_filter_get_config(ir_filter *h, ir_dtype dtype, int k, ir_kernel_config *out) {
   if (!h || !out) return fail(h, IR_EINVAL, "null argument");
   if (!valid_dtype(dtype) || !valid_k(k)) return fail(h, IR_EINVAL, "bad dtype or k");
@@ -587,6 +600,7 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     cl.prm.tile_h = cl.cfg.tile_h;
     cl.prm.status = h->d_status;
     cl.prm.launches = h->d_launches;
+    cl.prm.mode = h->detector;
     cl.prm.border = h->border;
     ir_status s = host_prepare_class(h, cl);
     if (s != IR_OK) return s;
@@ -681,10 +695,12 @@ ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, v
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
   PlanKey key;
-  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border));
+  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
   std::memcpy(key.bytes.data(), descs, sizeof(ir_frame_desc) * n);
   std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n, h->cfg, sizeof(h->cfg));
   std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n + sizeof(h->cfg), &h->border, sizeof(h->border));
+  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border), &h->detector,
+              sizeof(h->detector));
   auto it = h->plans.find(key);
   ir_batch_plan *plan = nullptr;
   if (it != h->plans.end()) {

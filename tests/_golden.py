@@ -10,6 +10,7 @@ _DT = {"u8": (np.uint8, 0), "u16": (np.uint16, 1), "u14": (np.uint16, 2)}
 
 def load(path):
     k = dtype = flagged = None
+    detector = "extreme"
     sect = None
     rows = {"input": [], "output": []}
     with open(path) as fh:
@@ -22,6 +23,8 @@ def load(path):
                 k = int(head[1])
             elif head[0] == "dtype":
                 dtype = head[1]
+            elif head[0] == "detector":
+                detector = head[1]
             elif head[0] in ("input", "output"):
                 sect = head[0]
             elif head[0] == "flagged":
@@ -37,8 +40,11 @@ def load(path):
         "input": np.array(rows["input"], dtype=npdt),
         "output": np.array(rows["output"], dtype=npdt),
         "flagged": flagged,
+        "detector": detector,   # "extreme" (Eq. 3a/3b) or "directional" (Fig. 1)
     }
 
 
-def all_fixtures():
-    return [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))]
+def all_fixtures(detector=None):
+    """Every fixture, or those of one detector ("extreme" or "directional")."""
+    fx = [load(p) for p in sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))]
+    return [f for f in fx if detector is None or f["detector"] == detector]

@@ -151,3 +151,90 @@ def test_detail_retention_report(flt):
         for label in ("fnr", "mf"):
             r = res[k][label]["structure"]
             assert r["pixels"] > 1000 and 0.0 <= r["kept"] <= 1.0
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 9, 11, 15, 21])
+def test_directional_detector_matches_oracle(flt, k):
+    """The directional detector (Fig. 1) through every strategy, each border
+    reading, TMA-staged and plain-staged frames, frames smaller than the
+    window, u8 / u16 / 14-bit synthetic frames; flagged counts included."""
+    import torch
+    rng = np.random.default_rng(70 + k)
+    flt.set_detector("directional")
+    assert flt.get_detector() == _lib.IR_DETECT_DIRECTIONAL
+    try:
+        for border in ("replicate", "mirror", "zero"):
+            flt.set_border(border)
+            for es, dt in ((1, _lib.IR_U8), (2, _lib.IR_U16), (2, _lib.IR_U14)):
+                npdt = np.uint8 if es == 1 else np.uint16
+                for algo in _algos(k):
+                    flt.set_config(dt, k, 64, 64, algo)
+                    cases = [(70, 133, 144), (70, 133, 137), (5, 3, 16), (1, 40, 48), (130, 64, 64)]
+                    for H, W, pitch in cases:
+                        if dt == _lib.IR_U14:
+                            a = synth.make_frame(H, W, synth.U14, H * 1000 + W + k, 8.0, 0.2)
+                        else:
+                            a = rng.integers(0, 256 if es == 1 else 65536, (H, W)).astype(npdt)
+                        want, wf = oracle.fnr_directional(a, k, border)
+                        ib, ia, ip = upload(a, pitch)
+                        ob, oa, op = empty_like_frame(a, pitch)
+                        ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+                        flt.ir_filter_run2(ia, ip, oa, op, H, W, dt, k, None, ctr)
+                        got = download(ob, oa, op, H, W, npdt)
+                        np.testing.assert_array_equal(got, want,
+                                                      err_msg=f"{border} k{k} dt{dt} algo{algo} {H}x{W} p{pitch}")
+                        assert int(ctr.item()) == wf
+                flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+    finally:
+        flt.set_detector("extreme")
+        flt.set_border("replicate")
+    assert flt.get_detector() == _lib.IR_DETECT_EXTREME
+
+
+def test_directional_detector_full_size_batch_and_passes(flt):
+    """Full-size sweep frames (640 x 512, 14-bit, 5-40% impulses, k = 3/5/7)
+    in one batch with a 640 x 512 random-valued frame at k = 13, and two
+    iterative passes, all with the directional detector."""
+    import torch
+    flt.set_detector("directional")
+    try:
+        specs = synth.workload_sweep_u14()
+        frames = [(s.make(), s.k) for s in specs[::2]]
+        frames.append((synth.make_frame(512, 640, synth.U14, 73, 8.0, 0.2, impulse="rv"), 13))
+        staged = []
+        for f, k in frames:
+            ib, ia, ip = upload(f)
+            ob, oa, op = empty_like_frame(f)
+            ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+            staged.append((f, k, ib, ia, ip, ob, oa, op, ctr))
+        arr = (_lib.ir_frame_desc * len(staged))()
+        for i, (f, k, ib, ia, ip, ob, oa, op, ctr) in enumerate(staged):
+            arr[i].in_, arr[i].out = ia, oa
+            arr[i].H, arr[i].W = f.shape
+            arr[i].in_pitch, arr[i].out_pitch = ip, op
+            arr[i].dtype, arr[i].k = _lib.IR_U14, k
+            arr[i].flagged_count = int(ctr.data_ptr())
+        flt.ir_filter_run_batch(arr, len(staged))
+        torch.cuda.synchronize()
+        for f, k, ib, ia, ip, ob, oa, op, ctr in staged:
+            want, wf = oracle.fnr_directional(f, k)
+            np.testing.assert_array_equal(download(ob, oa, op, f.shape[0], f.shape[1], f.dtype), want)
+            assert int(ctr.item()) == wf
+        # two passes: the second filters the first's output
+        f, k = frames[0]
+        first, f1 = oracle.fnr_directional(f, k)
+        second, f2 = oracle.fnr_directional(first, k)
+        ib, ia, ip = upload(f)
+        ob, oa, op = empty_like_frame(f)
+        ctr = torch.zeros(2, dtype=torch.int64, device="cuda")
+        flt.ir_filter_run_passes(ia, ip, oa, op, f.shape[0], f.shape[1], _lib.IR_U14, k, 2, None, ctr)
+        np.testing.assert_array_equal(download(ob, oa, op, f.shape[0], f.shape[1], f.dtype), second)
+        assert [int(v) for v in ctr.cpu().tolist()] == [f1, f2]
+    finally:
+        flt.set_detector("extreme")
+
+
+def test_detector_rejects_unknown_code(flt):
+    with pytest.raises(_lib.IrError):
+        flt.set_detector(7)
+    assert flt.get_detector() == _lib.IR_DETECT_EXTREME

@@ -99,7 +99,11 @@ def test_golden_fixtures_every_algo(flt, fx):
     for algo in algos_for(k):
         for dt in ((_lib.IR_U8,) if es == 1 else (_lib.IR_U16, _lib.IR_U14)):
             with_config(flt, dt, k, algo, 64, 64)
-        got, gf = gpu_fnr(flt, fx["input"], k, u14=(fx["dtype"] == _lib.IR_U14))
+        flt.set_detector(fx["detector"])
+        try:
+            got, gf = gpu_fnr(flt, fx["input"], k, u14=(fx["dtype"] == _lib.IR_U14))
+        finally:
+            flt.set_detector("extreme")
         np.testing.assert_array_equal(got, fx["output"])
         assert gf == fx["flagged"]
     flt.set_config(_lib.IR_U8, k, 0, 0, _lib.IR_ALGO_AUTO)

@@ -90,14 +90,17 @@ def test_median_rank_matches_numpy_partition(oracle_mod):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("fx", all_fixtures(), ids=lambda f: f["name"])
 def test_golden_fixture(oracle_mod, fx):
-    out, flagged = oracle_mod.fnr(fx["input"], fx["k"])
+    if fx["detector"] == "directional":
+        out, flagged = oracle_mod.fnr_directional(fx["input"], fx["k"])
+    else:
+        out, flagged = oracle_mod.fnr(fx["input"], fx["k"])
     np.testing.assert_array_equal(out, fx["output"])
     assert flagged == fx["flagged"]
 
 
 def test_golden_fixtures_present():
-    names = [f["name"] for f in all_fixtures()]
-    assert len(names) >= 6
+    assert len(all_fixtures("extreme")) >= 6
+    assert len(all_fixtures("directional")) >= 3
 
 
 # ---------------------------------------------------------------------------
@@ -388,7 +391,7 @@ def slow_fnr(a, k, border="nearest", strict=False, exclude_centre=False, rank_sh
 
 def _pins_pass(impl):
     """Run the golden and library pins against ``impl``; False at first failure."""
-    for fx in all_fixtures():
+    for fx in all_fixtures("extreme"):
         o, f = impl(fx["input"], fx["k"])
         if not np.array_equal(o, fx["output"]) or f != fx["flagged"]:
             return False
