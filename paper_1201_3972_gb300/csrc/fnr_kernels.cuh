@@ -1084,9 +1084,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
 
   if (warp == kConsumerWarps) {
     // ------------------------------------------------------------- producer
-    // Tiles are handed out by an atomic counter when the launch has one (tiles
-    // differ in cost: a strip's median work grows with its flagged pixels),
-    // else in static round robin.
+    // Tiles are handed out by an atomic counter when the launch has one and
+    // more tiles than CTAs (tiles differ in cost: a strip's median work grows
+    // with its flagged pixels), else in static round robin. A CTA's first tile
+    // is its own index either way, so no atomic precedes the first load; the
+    // counter hands out the tiles after the grid's first ones.
+    const bool dynamic = p.sched != nullptr && static_cast<int>(gridDim.x) < p.total_tiles;
     for (int i = 0;; ++i) {
       const int s = i % NS, use = i / NS;
       // the stage's previous tile (i - NS) must be released by every consumer warp
@@ -1095,10 +1098,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         break;
       }
       int tile = blockIdx.x + i * static_cast<int>(gridDim.x);
-      if (p.sched != nullptr) {
+      if (dynamic && i > 0) {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(&p.sched[0], 1u);
-        tile = static_cast<int>(min(__shfl_sync(0xffffffffu, t, 0), 0x7fffffffu));
+        tile = static_cast<int>(min(__shfl_sync(0xffffffffu, t, 0) + gridDim.x, 0x7fffffffu));
       }
       const TileInfo ti = locate_tile(p, dir, tile);
       T *const S = stage_ptr(s);
@@ -1123,7 +1126,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         if (lane == 0) mbar_arrive(&full[s]);
       }
     }
-    if (p.sched != nullptr && lane == 0) {
+    if (dynamic && lane == 0) {
       // this CTA takes no more tiles; the last CTA to get here resets the slot
       __threadfence();
       if (atomicAdd(&p.sched[1], 1u) == gridDim.x - 1) {

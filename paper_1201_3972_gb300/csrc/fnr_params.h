@@ -43,9 +43,12 @@ struct alignas(128) FnrParams {
   int tile_w, tile_h;
   unsigned int *status;            // device status word (bit 0: bounded wait timed out)
   unsigned long long *launches;    // device launch counter (nullable)
-  // dynamic tile order (nullable: static round robin): sched[0] hands out tile
-  // indices, sched[1] counts CTAs that are done; the last CTA zeroes both, so
-  // a slot is ready for the next launch ordered after this one
+  // dynamic tile order (nullable: static round robin): each CTA's first tile
+  // is its block index; when there are more tiles than CTAs, sched[0] hands
+  // out the rest (tile gridDim.x + counter), sched[1] counts CTAs that are
+  // done, and the last CTA zeroes both, so a slot is ready for the next
+  // launch ordered after this one (a launch with no more tiles than CTAs
+  // leaves the slot untouched)
   unsigned int *sched;
   int mode;                        // kModeFnr, kModeMedian or kModeDirectional: which pixels are noisy
   int border;                      // kBorderReplicate / kBorderMirror / kBorderZero
