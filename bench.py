@@ -144,10 +144,27 @@ def build_workload(replicas: int):
     return specs, frames
 
 
-def time_events(torch, fn, steps: int, stream) -> list:
-    """Per-step durations (ms) measured with CUDA events on `stream`."""
+LEG_ITERS = 100   # timed iterations of each side leg (median reported)
+_flush_buf = None
+
+
+def flush_l2(torch, stream):
+    """Overwrite a buffer twice the size of L2 on `stream`, so the next timed
+    launch finds none of its inputs or outputs in L2."""
+    global _flush_buf
+    if _flush_buf is None:
+        _flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        _flush_buf.fill_(0)
+
+
+def time_events(torch, fn, steps: int, stream, flush: bool = False) -> list:
+    """Per-step durations (ms) measured with CUDA events on `stream`; with
+    `flush`, L2 is flushed before every step, outside the events."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in evs:
+        if flush:
+            flush_l2(torch, stream)
         a.record(stream)
         fn()
         b.record(stream)
@@ -237,7 +254,7 @@ def own_arm(args):
         sub = _lib.BatchPlan(flt, descs_for(idx))
         for _ in range(args.warmup):
             sub.launch(stream)
-        durs = time_events(torch, lambda: sub.launch(stream), max(args.steps, 5), stream)
+        durs = time_events(torch, lambda: sub.launch(stream), max(args.steps, LEG_ITERS), stream, flush=True)
         ms = statistics.median(durs)
         px = len(idx) * fpx
         algo_bytes = px * 2 * 2  # read + write, 2 bytes per pixel
@@ -266,7 +283,8 @@ def own_arm(args):
                 sub = _lib.BatchPlan(flt, descs_for(idx))
                 for _ in range(args.warmup):
                     sub.launch(stream)
-                ms = statistics.median(time_events(torch, lambda: sub.launch(stream), max(args.steps, 5), stream))
+                ms = statistics.median(time_events(torch, lambda: sub.launch(stream), max(args.steps, LEG_ITERS),
+                                                   stream, flush=True))
                 sub.close()
                 ctr = torch.zeros(1, dtype=torch.int64, device=dev)
                 counted = _lib.BatchPlan(flt, descs_for(idx, int(ctr.data_ptr())))
@@ -349,7 +367,9 @@ def own_arm(args):
                    "replicas": R, "mpx_per_step": round(step_px / 1e6, 3),
                    "l2": (f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step > 129 MB L2 (no flush needed)"
                           if nframes * frame_bytes > L2_BYTES else
-                          f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step fit in the 129 MB L2 (small run)"),
+                          f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step fit in the 129 MB L2 (small run)")
+                   + f"; side legs (per_k, directional, batch, large k, single frame) write {2 * L2_BYTES // 10**6} MB"
+                   f" before each of their {LEG_ITERS} timed iterations to flush L2",
                    "parallelism": f"frames sharded per GPU (dp{world}), no collective"},
         "roofline": roofline,
         "per_k": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
@@ -405,7 +425,7 @@ def batch_leg(flt, stream, args):
                          for i in idx])
         for _ in range(args.warmup):
             plan.launch(stream)
-        durs = time_events(torch, lambda: plan.launch(stream), max(5, args.steps), stream)
+        durs = time_events(torch, lambda: plan.launch(stream), max(LEG_ITERS, args.steps), stream, flush=True)
         ms = statistics.median(durs)
         px = sum(specs[i].pixels for i in idx)
         byts = sum(2 * specs[i].pixels * specs[i].esize for i in idx)
@@ -435,7 +455,7 @@ def single_frame_leg(flt, stream, args):
                            stream.cuda_stream, None)
     for _ in range(max(3, args.warmup)):
         once()
-    dev_us = 1e3 * statistics.median(time_events(torch, once, 50, stream))
+    dev_us = 1e3 * statistics.median(time_events(torch, once, LEG_ITERS, stream, flush=True))
     torch.cuda.synchronize()
     walls = []
     for _ in range(50):
@@ -475,7 +495,8 @@ def large_k_leg(flt, stream, args):
         plan = _lib.BatchPlan(flt, arr)
         for _ in range(args.warmup):
             plan.launch(stream)
-        ms = statistics.median(time_events(torch, lambda: plan.launch(stream), max(5, args.steps), stream))
+        ms = statistics.median(time_events(torch, lambda: plan.launch(stream), max(LEG_ITERS, args.steps), stream,
+                                           flush=True))
         px = copies * H * W
         out[str(s.k)] = {"frames": copies, "ms": round(ms, 4), "mpx_s": round(px / ms / 1e3, 1),
                          "hbm_frac": round(px * 4 / (ms * 1e-3) / 1e9 / hbm, 4),
