@@ -396,6 +396,8 @@ def own_arm(args):
     if rank == 0 and args.serve_seconds > 0:
         result["serve"] = serve_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline:
+        plan.launch(stream)  # the output buffer holds the timed step's result, whatever the legs wrote since
+        torch.cuda.synchronize()
         result["cpu_baseline"], result["parity"] = cpu_baseline(frames, specs, d_out, fpx, args)
     if rank == 0:
         print(json.dumps(result), flush=True)
