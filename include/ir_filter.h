@@ -42,7 +42,8 @@ extern "C" {
 typedef enum {
   IR_OK = 0,
   IR_EINVAL = 1,        /* bad argument (k even/out of range, H or W < 1, NULL, pitch too small, overlap) */
-  IR_EALIGN = 2,        /* reserved: alignment is never an error (unaligned frames take a plain-load path) */
+  IR_EALIGN = 2,        /* strict alignment only (ir_filter_set_strict_alignment): a frame's base or pitch is not
+                           16-byte aligned; otherwise such frames take a plain-load path and are no error */
   IR_ENOMEM = 3,        /* device scratch could not be grown / admission refused for lack of memory */
   IR_ECUDA = 4,         /* a CUDA runtime call failed (see ir_filter_last_error) */
   IR_ETIMEOUT = 5,      /* a bounded device-side wait gave up (reported by ir_filter_sync_status) */
@@ -188,6 +189,15 @@ ir_status ir_filter_sync_status(ir_filter *h);
  * ir_filter_run_noalloc and the server always replicate. */
 ir_status ir_filter_set_border(ir_filter *h, ir_border mode);
 ir_border ir_filter_get_border(const ir_filter *h);
+
+/* Strict alignment for the handle's later calls (on != 0): every frame's base
+ * address and row pitch, input and output, must be multiples of 16 bytes,
+ * which the TMA tile copies need, or the call returns IR_EALIGN and launches
+ * nothing (a batch plan is refused when any frame fails). Off (the default),
+ * such frames are staged and written with plain loads and stores instead.
+ * Frames whose row (W * bytes per pixel) is not a multiple of 16 bytes are
+ * accepted either way (their right-edge tiles use plain stores). */
+ir_status ir_filter_set_strict_alignment(ir_filter *h, int on);
 
 /* Noise detector for the handle's later calls, like ir_filter_set_border
  * (single frames, in place, passes, batch plans created afterwards; tuning

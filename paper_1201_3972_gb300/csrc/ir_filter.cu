@@ -71,6 +71,7 @@ struct ir_filter {
   ir_kernel_config cfg[2][kNumK];
   int border = kBorderReplicate;
   int detector = kModeFnr;  // kModeFnr (Eq. 3a/3b) or kModeDirectional
+  bool strict_align = false;  // misaligned frames are refused (IR_EALIGN) instead of staged with plain loads
   std::string last_error;
   std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, smem) -> CTAs per SM
   std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
@@ -191,6 +192,8 @@ static bool ranges_overlap(const void *a, size_t a_len, const void *b, size_t b_
   return pa < pb + b_len && pb < pa + a_len;
 }
 
+static bool tma_addressable(const void *p, size_t pitch);
+
 static ir_status check_frame(ir_filter *h, const void *in, size_t in_pitch, const void *out, size_t out_pitch, int H,
                              int W, int dtype, int k) {
   if (!in || !out) return fail(h, IR_EINVAL, "null frame pointer");
@@ -202,6 +205,8 @@ static ir_status check_frame(ir_filter *h, const void *in, size_t in_pitch, cons
   if (static_cast<long long>(H) * W > (1LL << 40)) return fail(h, IR_EINVAL, "frame too large");
   const size_t in_len = (H - 1) * in_pitch + row, out_len = (H - 1) * out_pitch + row;
   if (ranges_overlap(in, in_len, out, out_len)) return fail(h, IR_EINVAL, "input and output overlap");
+  if (h && h->strict_align && (!tma_addressable(in, in_pitch) || !tma_addressable(out, out_pitch)))
+    return fail(h, IR_EALIGN, "strict alignment: frame base or pitch is not a multiple of 16 bytes");
   return IR_OK;
 }
 
@@ -511,6 +516,12 @@ ir_status ir_filter_set_border(ir_filter *h, ir_border mode) {
 
 ir_border ir_filter_get_border(const ir_filter *h) {
   return h ? static_cast<ir_border>(h->border) : IR_BORDER_REPLICATE;
+}
+
+ir_status ir_filter_set_strict_alignment(ir_filter *h, int on) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  h->strict_align = on != 0;
+  return IR_OK;
 }
 
 ir_status ir_filter_set_detector(ir_filter *h, ir_detector detector) {

@@ -66,6 +66,10 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ir_filter_run_batch(None, None, 0, None) == _lib.IR_EINVAL
     assert lib.ir_filter_sync_status(None) == _lib.IR_EINVAL
     assert lib.ir_filter_launch_count(None) == 0
+    assert lib.ir_filter_set_border(None, 0) == _lib.IR_EINVAL
+    assert lib.ir_filter_set_detector(None, 0) == _lib.IR_EINVAL
+    assert lib.ir_filter_set_strict_alignment(None, 1) == _lib.IR_EINVAL
+    assert lib.ir_filter_get_detector(None) == _lib.IR_DETECT_EXTREME
     lib.ir_filter_destroy(None)
     lib.ir_batch_plan_destroy(None)
 

@@ -256,6 +256,42 @@ def test_errors_are_reported(flt):
     flt.sync_status()
 
 
+def test_strict_alignment_refuses_misaligned_frames(flt):
+    """With strict alignment a misaligned base or pitch (input or output,
+    single frames, in place and batches) is IR_EALIGN and nothing is written;
+    aligned frames still run, and turning it off restores the plain path."""
+    import torch
+    rng = np.random.default_rng(11)
+    a = rng.integers(0, 256, (40, 70)).astype(np.uint8)
+    flt.set_strict_alignment(True)
+    try:
+        for kw in (dict(in_pitch=73), dict(out_pitch=75), dict(in_off=1, in_pitch=80), dict(out_off=2, out_pitch=80)):
+            ib, ia, ip = upload(a, kw.get("in_pitch"), kw.get("in_off", 0))
+            ob, oa, op = empty_like_frame(a, kw.get("out_pitch"), kw.get("out_off", 0))
+            before = ob.clone()
+            with pytest.raises(_lib.IrError) as e:
+                flt.ir_filter_run2(ia, ip, oa, op, 40, 70, _lib.IR_U8, 3)
+            assert e.value.status == _lib.IR_EALIGN
+            torch.cuda.synchronize()
+            assert torch.equal(ob, before)
+        ib, ia, ip = upload(a, 75)
+        with pytest.raises(_lib.IrError) as e:
+            flt.ir_filter_run(ia, 40, 70, ip, _lib.IR_U8, 3)
+        assert e.value.status == _lib.IR_EALIGN
+        arr = (_lib.ir_frame_desc * 1)()
+        ob, oa, op = empty_like_frame(a, 80)
+        arr[0].in_, arr[0].out, arr[0].H, arr[0].W = ia, oa, 40, 70
+        arr[0].in_pitch, arr[0].out_pitch, arr[0].dtype, arr[0].k = ip, op, _lib.IR_U8, 5
+        with pytest.raises(_lib.IrError) as e:
+            flt.ir_filter_run_batch(arr, 1)
+        assert e.value.status == _lib.IR_EALIGN
+        check(flt, a, 3, in_pitch=80, out_pitch=96)   # aligned: runs
+    finally:
+        flt.set_strict_alignment(False)
+    check(flt, a, 3, in_pitch=73, out_pitch=75)       # off again: the plain path
+    flt.sync_status()
+
+
 def test_autotune_keeps_results_exact(flt):
     f = synth.workload_sweep_u14()[1].make()
     for k in (3, 5, 9):
