@@ -48,7 +48,9 @@ typedef enum {
   IR_ECUDA = 4,         /* a CUDA runtime call failed (see ir_filter_last_error) */
   IR_ETIMEOUT = 5,      /* a bounded device-side wait gave up (reported by ir_filter_sync_status) */
   IR_EBUSY = 6,         /* no free slot right now (server admission) */
-  IR_EUNSUPPORTED = 7   /* configuration not built into this library */
+  IR_EUNSUPPORTED = 7,  /* configuration not built into this library */
+  IR_ECHECK = 8         /* debug builds (FNR_DEBUG_CHECKS) only: an index or alignment check inside a kernel
+                           failed and the access was skipped (reported by ir_filter_sync_status) */
 } ir_status;
 
 /* Pixel types. IR_U14 is 16-bit storage whose values the caller promises are
@@ -181,7 +183,8 @@ ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pitch_bytes, i
 /* Read and clear the handle's device status word (synchronises the device).
  * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call;
  * the handle's tile-order counters are then zeroed as well, since a kernel
- * that gave up may have left its counter mid-count. */
+ * that gave up may have left its counter mid-count. In a debug build,
+ * IR_ECHECK if a kernel's internal index or alignment check failed. */
 ir_status ir_filter_sync_status(ir_filter *h);
 
 /* Border reading for the handle's later calls (single frames, passes, median

@@ -52,15 +52,28 @@ def _compile(src: str, obj: str, extra) -> None:
     os.replace(obj + ".tmp", obj)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link libirfnr.so; returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+DEBUG_LIB_PATH = os.path.join(PKG, "libirfnr_debug.so")
+
+
+def build_debug(force: bool = False, verbose: bool = False) -> str:
+    """The same library with FNR_DEBUG_CHECKS: kernels check their list
+    indices, TMA coordinates and launch layout, record a failure in the status
+    word (IR_ECHECK) and skip the access. Built apart, as libirfnr_debug.so;
+    load it with IRFNR_LIBRARY=<path>. Returns its path."""
+    return build(force, verbose, extra_flags=("-DFNR_DEBUG_CHECKS",), out=DEBUG_LIB_PATH,
+                 build_dir=os.path.join(BUILD_DIR, "debug"))
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str = LIB_PATH,
+          build_dir: str = BUILD_DIR) -> str:
+    """Compile and link libirfnr.so (or `out`); returns its path."""
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdrs = _headers()
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD_DIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             jobs.append((s, o))
@@ -70,16 +83,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             futs = [ex.submit(_compile, s, o, extra_flags) for s, o in jobs]
             for f in futs:
                 f.result()
-    if force or jobs or _stale(LIB_PATH, objs):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
+    if force or jobs or _stale(out, objs):
+        tmp = out + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB_PATH)
+        os.replace(tmp, out)
     if verbose:
-        print(f"built {LIB_PATH}", file=sys.stderr)
-    return LIB_PATH
+        print(f"built {out}", file=sys.stderr)
+    return out
 
 
 if __name__ == "__main__":

@@ -16,7 +16,7 @@ from typing import Optional
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libirfnr.so")
 
-IR_OK, IR_EINVAL, IR_EALIGN, IR_ENOMEM, IR_ECUDA, IR_ETIMEOUT, IR_EBUSY, IR_EUNSUPPORTED = range(8)
+IR_OK, IR_EINVAL, IR_EALIGN, IR_ENOMEM, IR_ECUDA, IR_ETIMEOUT, IR_EBUSY, IR_EUNSUPPORTED, IR_ECHECK = range(9)
 IR_U8, IR_U16, IR_U14 = 0, 1, 2
 IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE = 0, 1, 2, 3
 IR_BORDER_REPLICATE, IR_BORDER_MIRROR, IR_BORDER_ZERO = 0, 1, 2
@@ -84,7 +84,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return LIB_PATH
+    """The library this process loads: ``libirfnr.so``, or the file named by
+    the IRFNR_LIBRARY environment variable (e.g. the debug-check build)."""
+    return os.environ.get("IRFNR_LIBRARY") or LIB_PATH
 
 
 def load(path: Optional[str] = None):
@@ -93,7 +95,7 @@ def load(path: Optional[str] = None):
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or library_path()
         if not os.path.exists(p):
             raise RuntimeError(f"CUDA library {p} is not built; run paper_1201_3972_gb300._build.build()")
         lib = ctypes.CDLL(p)

@@ -1038,6 +1038,33 @@ struct SparseLimit {
 // ---------------------------------------------------------------------------
 // The kernel.
 // ---------------------------------------------------------------------------
+#ifdef FNR_DEBUG_CHECKS
+// Debug builds: a strip's flagged list must fit its capacity and every entry
+// must name a pixel of the strip (row < SR, column < TW), since the median
+// stages index the stage, the output tile and the bit planes with it. On a
+// violation the status word records it and the strip takes no medians.
+__device__ __forceinline__ int debug_check_list(const uint16_t *list, int F, int SR, int TW, unsigned *status, int lane) {
+  bool bad = F < 0 || F > SR * TW;
+  for (int j = lane; !bad && j < F; j += 32) {
+    const int e = list[j];
+    bad = (e >> 8) >= SR || (e & 255) >= TW;
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if (bad && lane == 0) atomicOr(status, kStatusCheck);
+  return bad ? 0 : F;
+}
+
+// Debug builds: a TMA box copy must start on a 16-byte boundary in x and at
+// a 128-byte aligned shared-memory address (the hardware faults otherwise),
+// and a store must not start above the frame.
+__device__ __forceinline__ bool debug_tma_ok(int x, int y, int esize, bool store, const void *smem_side,
+                                             unsigned *status) {
+  const bool ok = ((x * esize) & 15) == 0 && (!store || y >= 0) && (smem_addr(smem_side) & 127u) == 0;
+  if (!ok) atomicOr(status, kStatusCheck);
+  return ok;
+}
+#endif
+
 template <int ALGO, int K>
 struct MinBlocks {
   // the 81-input network of k = 9 needs about 96 registers
@@ -1079,6 +1106,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     }
     fence_mbar_init();
     if (blockIdx.x == 0 && p.launches != nullptr) atomicAdd(p.launches, 1ull);
+#ifdef FNR_DEBUG_CHECKS
+    // the launch provides the layout's shared memory, and the tile splits
+    // into the consumer warps' strips
+    uint32_t dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (dyn < static_cast<uint32_t>(L.total) || SR * kConsumerWarps != TH || TW % 8 != 0)
+      atomicOr(p.status, kStatusCheck);
+#endif
   }
   __syncthreads();  // the only block-wide barrier
 
@@ -1113,7 +1148,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
       }
       const int xs = ti.x0 - XOFF;
       const int ys = ti.y0 - R;
-      if (ti.flags & kFrameTmaIn) {
+      bool tma_load = (ti.flags & kFrameTmaIn) != 0;
+#ifdef FNR_DEBUG_CHECKS
+      if (tma_load)
+        tma_load = __shfl_sync(0xffffffffu, lane == 0 ? debug_tma_ok(xs, ys, E, false, S, p.status) : true, 0);
+#endif
+      if (tma_load) {
         if (lane == 0) {
           fence_proxy_async_smem();
           mbar_arrive_expect_tx(&full[s], box_bytes);
@@ -1185,11 +1225,19 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     const bool tma_in = (cur.flags & kFrameTmaIn) != 0;
     // A TMA store clips the box at the frame edge in whole 16-byte units, so a
     // right-edge tile of a frame whose row is not a multiple of 16 bytes would
-    // touch the bytes between W and the pitch: such tiles use plain stores.
+    // touch the bytes between W and the pitch: such tiles use plain stores. A
+    // TMA copy also needs its shared-memory side 128-byte aligned, so each
+    // warp's strip of the output tile (SR rows of TW pixels) must be a
+    // multiple of 128 bytes; smaller tiles store their strips with plain stores.
     const bool ragged_right = x0 + TW > cur.W && ((cur.W * E) & 15) != 0;
-    const bool tma_out = (cur.flags & kFrameTmaOut) != 0 && !ragged_right;
+    bool tma_out = (cur.flags & kFrameTmaOut) != 0 && !ragged_right && ((SR * TW * E) & 127) == 0;
     T *const S = stage_ptr(s);
     T *const O = (i & 1) ? out1 : out0;  // output tiles alternate independently of the stage ring
+#ifdef FNR_DEBUG_CHECKS
+    if (ALGO != ALGO_DENSE3 && tma_out)
+      tma_out = __shfl_sync(0xffffffffu, lane == 0 ? debug_tma_ok(x0, y0 + r0, E, true, O + r0 * TW, p.status) : true,
+                            0);
+#endif
     const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
     if (live && ALGO == ALGO_DENSE3) {
@@ -1247,6 +1295,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         __syncwarp();
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
                                          p.mode, divG, PackedOp{p.unit, 0u - p.unit}, lane);
+#ifdef FNR_DEBUG_CHECKS
+        flagged = debug_check_list(list, flagged, SR, TW, p.status, lane);
+#endif
       }
       if (lane == 0) {
         counts[s * kConsumerWarps + warp] = flagged;
@@ -1287,6 +1338,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         __syncwarp();
         flagged = horizontal_pairs<T, K>(S, vmin, vmax, O, list, TW, BW, L.nps, r0, SR, cur.W - x0, cur.H - y0,
                                          p.mode, divG, PackedOp{p.unit, 0u - p.unit}, lane);
+#ifdef FNR_DEBUG_CHECKS
+        flagged = debug_check_list(list, flagged, SR, TW, p.status, lane);
+#endif
         if constexpr (ALGO == ALGO_NETWORK) {
           network_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane, PackedOp{p.unit, 0u - p.unit});
         } else if (flagged <= SparseLimit<K>::value) {

@@ -67,6 +67,9 @@ constexpr int kModeMedian = 1;     // standard median filter: replace every pixe
 constexpr int kModeDirectional = 2;
 
 constexpr unsigned int kStatusTimeout = 1u;
+// builds with FNR_DEBUG_CHECKS: an internal index or alignment check failed
+// in a kernel, which skipped the access (or took the plain path) instead
+constexpr unsigned int kStatusCheck = 2u;
 
 __host__ __device__ constexpr int align_up(int v, int a) { return (v + a - 1) / a * a; }
 

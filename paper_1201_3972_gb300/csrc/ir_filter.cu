@@ -355,6 +355,7 @@ const char *ir_status_string(ir_status s) {
     case IR_ETIMEOUT: return "device-side wait timed out";
     case IR_EBUSY: return "busy";
     case IR_EUNSUPPORTED: return "unsupported configuration";
+    case IR_ECHECK: return "internal check failed in a kernel (debug build)";
   }
   return "unknown status";
 }
@@ -492,6 +493,7 @@ ir_status ir_filter_sync_status(ir_filter *h) {
     IR_CUDA(h, cudaMemset(h->d_sched, 0, 2 * sizeof(unsigned) * kSchedSlots));
     return fail(h, IR_ETIMEOUT, "a bounded device-side wait gave up");
   }
+  if (st & kStatusCheck) return fail(h, IR_ECHECK, "an index or alignment check inside a kernel failed");
   return IR_OK;
 }
 

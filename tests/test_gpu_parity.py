@@ -135,6 +135,31 @@ def test_every_algo_and_tile_random(flt, k, es):
     flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
 
 
+@pytest.mark.parametrize("k", ALL_K)
+@pytest.mark.parametrize("es", [1, 2])
+def test_every_algo_and_tile_on_the_tma_path(flt, k, es):
+    """The same (algo, tile) sweep with 16-byte aligned bases and pitches, so
+    that tiles are staged and strips stored by TMA (strips smaller than 128
+    bytes store with plain stores, since a TMA copy needs its shared-memory
+    side 128-byte aligned)."""
+    rng = np.random.default_rng(2000 * k + es)
+    dt = _lib.IR_U8 if es == 1 else _lib.IR_U16
+    npdt = np.uint8 if es == 1 else np.uint16
+    maxv = 255 if es == 1 else 65535
+    for algo in algos_for(k):
+        for tw, th in tiles_for(es, k, algo):
+            try:
+                flt.set_config(dt, k, tw, th, algo)
+            except _lib.IrError as e:
+                assert e.status == _lib.IR_EINVAL
+                continue
+            for H, W in ((67, 150), (33, 29)):
+                pitch = -(-W * es // 16) * 16 // es
+                check(flt, rng.integers(0, maxv + 1, (H, W)).astype(npdt), k, in_pitch=pitch, out_pitch=pitch)
+    flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+    flt.sync_status()
+
+
 @pytest.mark.parametrize("k", [11, 15, 21])
 @pytest.mark.parametrize("es", [1, 2])
 def test_bitplane_sparse_and_dense_strips(flt, k, es):
