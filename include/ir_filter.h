@@ -154,6 +154,28 @@ typedef struct {
  * windows) is submitted again. Outputs must not overlap any input. */
 ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, void *cuda_stream);
 
+/* Frames in host memory: descs[i].in and descs[i].out are HOST addresses (the
+ * same descriptors as ir_filter_run_batch otherwise; flagged_count, if set, is
+ * a DEVICE address). Every frame is copied to device staging memory owned by
+ * the handle (rows padded to 16 bytes), the frames are filtered as batches,
+ * and the results are copied back. The frames go in `chunks` groups of whole
+ * frames (0 = 16; at most n; with four or more the two first and two last
+ * are a quarter and a half the size of the others, so the pipeline fills and
+ * drains quickly) through the handle's three
+ * streams (copies in, filtering, copies out), so that one chunk's copies
+ * overlap another's filtering and the two copy directions overlap each other; frames that lie back to back in host
+ * memory with rows of the padded size move as one copy. In place (in == out,
+ * same pitch) is allowed here; other overlaps are IR_EINVAL. Asynchronous on
+ * cuda_stream: the chunks start after the work already queued there, and the
+ * outputs are valid once cuda_stream is synchronised. Host memory should be
+ * pinned (cudaHostAlloc / cudaHostRegister) for full speed and asynchrony;
+ * pageable memory works, but its copies are staged by the driver and partly
+ * synchronous. The staging grows on demand (the handle then waits for its own
+ * earlier host-frame work): IR_ENOMEM if it cannot. Other errors as
+ * ir_filter_run_batch; strict alignment does not apply (the staging is
+ * aligned). Calls on one handle must not overlap from several host threads. */
+ir_status ir_filter_run_host(ir_filter *h, const ir_frame_desc *descs, int n, int chunks, void *cuda_stream);
+
 /* Explicit batch plans: validate and upload a descriptor set once, capture
  * its graph, then launch it any number of times. */
 typedef struct ir_batch_plan ir_batch_plan;

@@ -33,6 +33,7 @@ EXPORTED = (
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
     "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
     "ir_filter_get_border", "ir_filter_set_detector", "ir_filter_get_detector", "ir_filter_set_strict_alignment",
+    "ir_filter_run_host",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
     "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
@@ -106,6 +107,7 @@ def load(path: Optional[str] = None):
             "ir_filter_run": ([vp, vp, i32, i32, sz, i32, i32, vp], i32),
             "ir_filter_run2": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
             "ir_filter_run_batch": ([vp, ctypes.POINTER(ir_frame_desc), i32, vp], i32),
+            "ir_filter_run_host": ([vp, ctypes.POINTER(ir_frame_desc), i32, i32, vp], i32),
             "ir_batch_plan_create": ([vp, ctypes.POINTER(ir_frame_desc), i32, ctypes.POINTER(vp)], i32),
             "ir_batch_plan_launch": ([vp, vp], i32),
             "ir_batch_plan_kernel_count": ([vp], i32),
@@ -310,6 +312,10 @@ class Filter:
 
     def ir_filter_run_batch(self, descs, n: int, stream=None) -> None:
         _check(self.lib, self.h, self.lib.ir_filter_run_batch(self.h, descs, n, _stream(stream)))
+
+    def ir_filter_run_host(self, descs, n: int, chunks: int = 0, stream=None) -> None:
+        """Frames in host memory (descriptor in/out are host addresses)."""
+        _check(self.lib, self.h, self.lib.ir_filter_run_host(self.h, descs, n, int(chunks), _stream(stream)))
 
     def run_batch(self, frames, stream=None) -> None:
         descs = self.make_descs(frames)

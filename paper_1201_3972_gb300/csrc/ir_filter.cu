@@ -51,6 +51,11 @@ bool valid_k(int k) { return k >= 3 && k <= kMaxK && (k & 1); }
 
 }  // namespace
 
+// ir_filter_run_host pipelines its chunks over three streams: host-to-device
+// copies, filtering, device-to-host copies
+constexpr int kHostStreams = 3;
+constexpr int kHostChunks = 16;  // its default number of pipeline chunks
+
 struct PlanKey {
   std::vector<unsigned char> bytes;
   bool operator<(const PlanKey &o) const { return bytes < o.bytes; }
@@ -77,6 +82,14 @@ struct ir_filter {
   std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
   std::map<PlanKey, ir_batch_plan *> plans;               // ir_filter_run_batch cache
   std::vector<PlanKey> plan_order;                        // LRU, oldest first
+  // ir_filter_run_host: copy streams, device staging and one plan per chunk
+  cudaStream_t host_streams[kHostStreams] = {};
+  cudaEvent_t host_start = nullptr, host_done = nullptr;
+  std::vector<cudaEvent_t> host_events;  // per chunk: copied in, filtered
+  unsigned char *host_stage = nullptr;
+  size_t host_stage_bytes = 0;
+  std::vector<PlanKey> host_keys;
+  std::vector<ir_batch_plan *> host_plans;
 };
 
 struct ir_batch_plan {
@@ -195,7 +208,7 @@ static bool ranges_overlap(const void *a, size_t a_len, const void *b, size_t b_
 static bool tma_addressable(const void *p, size_t pitch);
 
 static ir_status check_frame(ir_filter *h, const void *in, size_t in_pitch, const void *out, size_t out_pitch, int H,
-                             int W, int dtype, int k) {
+                             int W, int dtype, int k, bool host_frame = false) {
   if (!in || !out) return fail(h, IR_EINVAL, "null frame pointer");
   if (H < 1 || W < 1) return fail(h, IR_EINVAL, "H and W must be >= 1 (got %d x %d)", H, W);
   if (!valid_dtype(dtype)) return fail(h, IR_EINVAL, "unknown dtype %d", dtype);
@@ -204,8 +217,10 @@ static ir_status check_frame(ir_filter *h, const void *in, size_t in_pitch, cons
   if (in_pitch < row || out_pitch < row) return fail(h, IR_EINVAL, "pitch smaller than W * bytes per pixel");
   if (static_cast<long long>(H) * W > (1LL << 40)) return fail(h, IR_EINVAL, "frame too large");
   const size_t in_len = (H - 1) * in_pitch + row, out_len = (H - 1) * out_pitch + row;
-  if (ranges_overlap(in, in_len, out, out_len)) return fail(h, IR_EINVAL, "input and output overlap");
-  if (h && h->strict_align && (!tma_addressable(in, in_pitch) || !tma_addressable(out, out_pitch)))
+  // host frames are staged through separate device buffers, so one may be filtered in place
+  const bool same = host_frame && in == out && in_pitch == out_pitch;
+  if (!same && ranges_overlap(in, in_len, out, out_len)) return fail(h, IR_EINVAL, "input and output overlap");
+  if (!host_frame && h && h->strict_align && (!tma_addressable(in, in_pitch) || !tma_addressable(out, out_pitch)))
     return fail(h, IR_EALIGN, "strict alignment: frame base or pitch is not a multiple of 16 bytes");
   return IR_OK;
 }
@@ -400,6 +415,15 @@ void ir_batch_plan_destroy(ir_batch_plan *plan);
 void ir_filter_destroy(ir_filter *h) {
   if (!h) return;
   DeviceGuard g(h->device);
+  for (int i = 0; i < kHostStreams; ++i)
+    if (h->host_streams[i]) cudaStreamSynchronize(h->host_streams[i]);
+  for (ir_batch_plan *p : h->host_plans) ir_batch_plan_destroy(p);
+  for (int i = 0; i < kHostStreams; ++i)
+    if (h->host_streams[i]) cudaStreamDestroy(h->host_streams[i]);
+  for (cudaEvent_t e : h->host_events) cudaEventDestroy(e);
+  if (h->host_start) cudaEventDestroy(h->host_start);
+  if (h->host_done) cudaEventDestroy(h->host_done);
+  if (h->host_stage) cudaFree(h->host_stage);
   for (auto &kv : h->plans) ir_batch_plan_destroy(kv.second);
   h->plans.clear();
   if (h->scratch) cudaFree(h->scratch);
@@ -737,6 +761,178 @@ ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, v
     h->plan_order.push_back(key);
   }
   return ir_batch_plan_launch(plan, cuda_stream);
+}
+
+// Copies of one chunk between host frames and their device staging: runs of
+// frames that are contiguous on the host with a row pitch equal to the
+// staging pitch go as one copy, the others one 2-D copy each.
+static ir_status host_copies(ir_filter *h, const ir_frame_desc *d, const size_t *off, const size_t *dp, int a, int b,
+                             bool to_device, cudaStream_t st) {
+  int i = a;
+  while (i < b) {
+    const unsigned char *hp = static_cast<const unsigned char *>(to_device ? d[i].in : d[i].out);
+    const size_t hpitch = to_device ? d[i].in_pitch : d[i].out_pitch;
+    const size_t row = static_cast<size_t>(d[i].W) * esize_of(d[i].dtype);
+    if (hpitch != dp[i]) {
+      void *dev = h->host_stage + off[i];
+      IR_CUDA(h, to_device ? cudaMemcpy2DAsync(dev, dp[i], hp, hpitch, row, d[i].H, cudaMemcpyHostToDevice, st)
+                           : cudaMemcpy2DAsync(const_cast<unsigned char *>(hp), hpitch, dev, dp[i], row, d[i].H,
+                                               cudaMemcpyDeviceToHost, st));
+      ++i;
+      continue;
+    }
+    size_t bytes = static_cast<size_t>(d[i].H) * dp[i];
+    int j = i + 1;
+    while (j < b) {
+      const unsigned char *hq = static_cast<const unsigned char *>(to_device ? d[j].in : d[j].out);
+      const size_t qpitch = to_device ? d[j].in_pitch : d[j].out_pitch;
+      if (qpitch != dp[j] || hq != hp + bytes || off[j] != off[i] + bytes) break;
+      bytes += static_cast<size_t>(d[j].H) * dp[j];
+      ++j;
+    }
+    void *dev = h->host_stage + off[i];
+    IR_CUDA(h, to_device ? cudaMemcpyAsync(dev, hp, bytes, cudaMemcpyHostToDevice, st)
+                         : cudaMemcpyAsync(const_cast<unsigned char *>(hp), dev, bytes, cudaMemcpyDeviceToHost, st));
+    i = j;
+  }
+  return IR_OK;
+}
+
+ir_status ir_filter_run_host(ir_filter *h, const ir_frame_desc *descs, int n, int chunks, void *cuda_stream) {
+  fnr::NvtxRange nvtx_range("ir_filter_run_host");
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
+  for (int i = 0; i < n; ++i) {
+    const ir_frame_desc &d = descs[i];
+    ir_status s = check_frame(h, d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, d.dtype, d.k, true);
+    if (s != IR_OK) return s;
+  }
+  DeviceGuard g(h->device);
+  // staging: every input, then every output, back to back with rows padded to
+  // 16 bytes (so every frame starts 16-byte aligned, as TMA needs, and frames
+  // that lie back to back on the host do so here too)
+  std::vector<size_t> dp(n), in_off(n), out_off(n);
+  size_t total = 0;
+  for (int i = 0; i < n; ++i) {
+    dp[i] = (static_cast<size_t>(descs[i].W) * esize_of(descs[i].dtype) + 15) / 16 * 16;
+    in_off[i] = total;
+    total += static_cast<size_t>(descs[i].H) * dp[i];
+  }
+  for (int i = 0; i < n; ++i) out_off[i] = in_off[i] + total;
+  const size_t need = 2 * total;
+  if (!h->host_start) {
+    IR_CUDA(h, cudaEventCreateWithFlags(&h->host_start, cudaEventDisableTiming));
+    IR_CUDA(h, cudaEventCreateWithFlags(&h->host_done, cudaEventDisableTiming));
+    for (int i = 0; i < kHostStreams; ++i)
+      IR_CUDA(h, cudaStreamCreateWithFlags(&h->host_streams[i], cudaStreamNonBlocking));
+  }
+  if (h->host_stage_bytes < need) {
+    // nothing of the previous calls may still use the old staging or its plans
+    for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamSynchronize(h->host_streams[i]));
+    for (ir_batch_plan *p : h->host_plans) ir_batch_plan_destroy(p);
+    h->host_plans.clear();
+    h->host_keys.clear();
+    if (h->host_stage) cudaFree(h->host_stage);
+    h->host_stage = nullptr;
+    h->host_stage_bytes = 0;
+    if (cudaMalloc(&h->host_stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      h->host_stage = nullptr;
+      return fail(h, IR_ENOMEM, "cannot allocate %zu bytes of host-frame staging", need);
+    }
+    h->host_stage_bytes = need;
+  }
+  // chunks of whole frames; with four or more, the first two and the last
+  // two are a quarter and a half of the others, so that the pipeline fills
+  // and drains quickly (the copy-in of the first chunk and the filtering and
+  // copy-out of the last are not overlapped with anything)
+  const int C = std::max(1, std::min(chunks > 0 ? chunks : kHostChunks, n));
+  std::vector<double> cum(C);
+  {
+    double sum = 0;
+    for (int c = 0; c < C; ++c) {
+      const int edge = std::min(c, C - 1 - c);
+      sum += C < 4 ? 1.0 : (edge == 0 ? 1.0 : (edge == 1 ? 2.0 : 4.0));
+      cum[c] = sum;
+    }
+    for (double &x : cum) x /= sum;
+  }
+  std::vector<int> bounds{0};
+  {
+    size_t acc = 0;
+    for (int i = 0; i + 1 < n && static_cast<int>(bounds.size()) < C; ++i) {
+      acc += static_cast<size_t>(descs[i].H) * dp[i];
+      if (static_cast<double>(acc) >= cum[bounds.size() - 1] * static_cast<double>(total)) bounds.push_back(i + 1);
+    }
+    bounds.push_back(n);
+  }
+  const int used = static_cast<int>(bounds.size()) - 1;
+  if (static_cast<int>(h->host_plans.size()) < used) {
+    h->host_plans.resize(used, nullptr);
+    h->host_keys.resize(used);
+  }
+  while (static_cast<int>(h->host_events.size()) < 2 * used) {
+    cudaEvent_t e;
+    IR_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    h->host_events.push_back(e);
+  }
+  cudaStream_t caller = static_cast<cudaStream_t>(cuda_stream);
+  cudaStream_t s_in = h->host_streams[0], s_filter = h->host_streams[1], s_out = h->host_streams[2];
+  // the chunks start after the caller's queued work and after this handle's
+  // previous host-frame call (whose end host_done marks; waiting on it is a
+  // no-op before the first call), whatever stream that call was on, since
+  // they reuse its staging
+  for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamWaitEvent(h->host_streams[i], h->host_done, 0));
+  IR_CUDA(h, cudaEventRecord(h->host_start, caller));
+  for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamWaitEvent(h->host_streams[i], h->host_start, 0));
+  std::vector<ir_frame_desc> dd(n);
+  for (int i = 0; i < n; ++i) {
+    dd[i] = descs[i];
+    dd[i].in = h->host_stage + in_off[i];
+    dd[i].out = h->host_stage + out_off[i];
+    dd[i].in_pitch = dd[i].out_pitch = dp[i];
+  }
+  // chunk c: copied in on s_in, filtered on s_filter once in, copied out on
+  // s_out once filtered; each stream runs the chunks in order, so the copies
+  // of chunk c + 1 overlap the filtering of chunk c and the copy-out of c - 1
+  for (int c = 0; c < used; ++c) {
+    const int a = bounds[c], b = bounds[c + 1];
+    cudaEvent_t ev_in = h->host_events[2 * c], ev_filtered = h->host_events[2 * c + 1];
+    ir_status s = host_copies(h, descs, in_off.data(), dp.data(), a, b, true, s_in);
+    if (s != IR_OK) return s;
+    IR_CUDA(h, cudaEventRecord(ev_in, s_in));
+    IR_CUDA(h, cudaStreamWaitEvent(s_filter, ev_in, 0));
+    // the chunk's plan, rebuilt when its frames or the handle's settings change
+    PlanKey key;
+    key.bytes.resize(sizeof(ir_frame_desc) * (b - a) + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
+    unsigned char *kp = key.bytes.data();
+    std::memcpy(kp, dd.data() + a, sizeof(ir_frame_desc) * (b - a));
+    kp += sizeof(ir_frame_desc) * (b - a);
+    std::memcpy(kp, h->cfg, sizeof(h->cfg));
+    std::memcpy(kp + sizeof(h->cfg), &h->border, sizeof(h->border));
+    std::memcpy(kp + sizeof(h->cfg) + sizeof(h->border), &h->detector, sizeof(h->detector));
+    if (!h->host_plans[c] || !(h->host_keys[c] == key)) {
+      if (h->host_plans[c]) {
+        // the old plan may still run on one of the copy streams
+        for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamSynchronize(h->host_streams[i]));
+        ir_batch_plan_destroy(h->host_plans[c]);
+        h->host_plans[c] = nullptr;
+      }
+      s = ir_batch_plan_create(h, dd.data() + a, b - a, &h->host_plans[c]);
+      if (s != IR_OK) return s;
+      h->host_keys[c] = key;
+    }
+    s = ir_batch_plan_launch(h->host_plans[c], s_filter);
+    if (s != IR_OK) return s;
+    IR_CUDA(h, cudaEventRecord(ev_filtered, s_filter));
+    IR_CUDA(h, cudaStreamWaitEvent(s_out, ev_filtered, 0));
+    s = host_copies(h, descs, out_off.data(), dp.data(), a, b, false, s_out);
+    if (s != IR_OK) return s;
+  }
+  // the last copy-out follows every other step of the call
+  IR_CUDA(h, cudaEventRecord(h->host_done, s_out));
+  IR_CUDA(h, cudaStreamWaitEvent(caller, h->host_done, 0));
+  return IR_OK;
 }
 
 // ---------------------------------------------------------------------------
