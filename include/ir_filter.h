@@ -173,7 +173,10 @@ ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, v
  * synchronous. The staging grows on demand (the handle then waits for its own
  * earlier host-frame work): IR_ENOMEM if it cannot. Other errors as
  * ir_filter_run_batch; strict alignment does not apply (the staging is
- * aligned). Calls on one handle must not overlap from several host threads. */
+ * aligned). Descriptors are checked before anything is queued; after a later
+ * error (a failed copy or plan), the chunks already queued still run and
+ * cuda_stream is joined with them. Calls on one handle must not overlap from
+ * several host threads. */
 ir_status ir_filter_run_host(ir_filter *h, const ir_frame_desc *descs, int n, int chunks, void *cuda_stream);
 
 /* Explicit batch plans: validate and upload a descriptor set once, capture

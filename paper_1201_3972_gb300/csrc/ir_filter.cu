@@ -798,6 +798,10 @@ static ir_status host_copies(ir_filter *h, const ir_frame_desc *d, const size_t 
   return IR_OK;
 }
 
+static ir_status host_chunk(ir_filter *h, const ir_frame_desc *descs, const ir_frame_desc *dd, const size_t *in_off,
+                            const size_t *out_off, const size_t *dp, int a, int b, int c, cudaStream_t s_in,
+                            cudaStream_t s_filter, cudaStream_t s_out);
+
 ir_status ir_filter_run_host(ir_filter *h, const ir_frame_desc *descs, int n, int chunks, void *cuda_stream) {
   fnr::NvtxRange nvtx_range("ir_filter_run_host");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
@@ -895,44 +899,54 @@ ir_status ir_filter_run_host(ir_filter *h, const ir_frame_desc *descs, int n, in
   // chunk c: copied in on s_in, filtered on s_filter once in, copied out on
   // s_out once filtered; each stream runs the chunks in order, so the copies
   // of chunk c + 1 overlap the filtering of chunk c and the copy-out of c - 1
-  for (int c = 0; c < used; ++c) {
-    const int a = bounds[c], b = bounds[c + 1];
-    cudaEvent_t ev_in = h->host_events[2 * c], ev_filtered = h->host_events[2 * c + 1];
-    ir_status s = host_copies(h, descs, in_off.data(), dp.data(), a, b, true, s_in);
-    if (s != IR_OK) return s;
-    IR_CUDA(h, cudaEventRecord(ev_in, s_in));
-    IR_CUDA(h, cudaStreamWaitEvent(s_filter, ev_in, 0));
-    // the chunk's plan, rebuilt when its frames or the handle's settings change
-    PlanKey key;
-    key.bytes.resize(sizeof(ir_frame_desc) * (b - a) + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
-    unsigned char *kp = key.bytes.data();
-    std::memcpy(kp, dd.data() + a, sizeof(ir_frame_desc) * (b - a));
-    kp += sizeof(ir_frame_desc) * (b - a);
-    std::memcpy(kp, h->cfg, sizeof(h->cfg));
-    std::memcpy(kp + sizeof(h->cfg), &h->border, sizeof(h->border));
-    std::memcpy(kp + sizeof(h->cfg) + sizeof(h->border), &h->detector, sizeof(h->detector));
-    if (!h->host_plans[c] || !(h->host_keys[c] == key)) {
-      if (h->host_plans[c]) {
-        // the old plan may still run on one of the copy streams
-        for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamSynchronize(h->host_streams[i]));
-        ir_batch_plan_destroy(h->host_plans[c]);
-        h->host_plans[c] = nullptr;
-      }
-      s = ir_batch_plan_create(h, dd.data() + a, b - a, &h->host_plans[c]);
-      if (s != IR_OK) return s;
-      h->host_keys[c] = key;
-    }
-    s = ir_batch_plan_launch(h->host_plans[c], s_filter);
-    if (s != IR_OK) return s;
-    IR_CUDA(h, cudaEventRecord(ev_filtered, s_filter));
-    IR_CUDA(h, cudaStreamWaitEvent(s_out, ev_filtered, 0));
-    s = host_copies(h, descs, out_off.data(), dp.data(), a, b, false, s_out);
-    if (s != IR_OK) return s;
+  // chunks queued before an error still run; the caller's stream is joined
+  // with them either way
+  ir_status err = IR_OK;
+  for (int c = 0; c < used && err == IR_OK; ++c) {
+    err = host_chunk(h, descs, dd.data(), in_off.data(), out_off.data(), dp.data(), bounds[c], bounds[c + 1], c,
+                     s_in, s_filter, s_out);
   }
   // the last copy-out follows every other step of the call
   IR_CUDA(h, cudaEventRecord(h->host_done, s_out));
   IR_CUDA(h, cudaStreamWaitEvent(caller, h->host_done, 0));
-  return IR_OK;
+  return err;
+}
+
+// One chunk of ir_filter_run_host: copy in on s_in, filter on s_filter once
+// in, copy out on s_out once filtered.
+static ir_status host_chunk(ir_filter *h, const ir_frame_desc *descs, const ir_frame_desc *dd, const size_t *in_off,
+                            const size_t *out_off, const size_t *dp, int a, int b, int c, cudaStream_t s_in,
+                            cudaStream_t s_filter, cudaStream_t s_out) {
+  cudaEvent_t ev_in = h->host_events[2 * c], ev_filtered = h->host_events[2 * c + 1];
+  ir_status s = host_copies(h, descs, in_off, dp, a, b, true, s_in);
+  if (s != IR_OK) return s;
+  IR_CUDA(h, cudaEventRecord(ev_in, s_in));
+  IR_CUDA(h, cudaStreamWaitEvent(s_filter, ev_in, 0));
+  // the chunk's plan, rebuilt when its frames or the handle's settings change
+  PlanKey key;
+  key.bytes.resize(sizeof(ir_frame_desc) * (b - a) + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
+  unsigned char *kp = key.bytes.data();
+  std::memcpy(kp, dd + a, sizeof(ir_frame_desc) * (b - a));
+  kp += sizeof(ir_frame_desc) * (b - a);
+  std::memcpy(kp, h->cfg, sizeof(h->cfg));
+  std::memcpy(kp + sizeof(h->cfg), &h->border, sizeof(h->border));
+  std::memcpy(kp + sizeof(h->cfg) + sizeof(h->border), &h->detector, sizeof(h->detector));
+  if (!h->host_plans[c] || !(h->host_keys[c] == key)) {
+    if (h->host_plans[c]) {
+      // the old plan may still run on one of the copy streams
+      for (int i = 0; i < kHostStreams; ++i) IR_CUDA(h, cudaStreamSynchronize(h->host_streams[i]));
+      ir_batch_plan_destroy(h->host_plans[c]);
+      h->host_plans[c] = nullptr;
+    }
+    s = ir_batch_plan_create(h, dd + a, b - a, &h->host_plans[c]);
+    if (s != IR_OK) return s;
+    h->host_keys[c] = key;
+  }
+  s = ir_batch_plan_launch(h->host_plans[c], s_filter);
+  if (s != IR_OK) return s;
+  IR_CUDA(h, cudaEventRecord(ev_filtered, s_filter));
+  IR_CUDA(h, cudaStreamWaitEvent(s_out, ev_filtered, 0));
+  return host_copies(h, descs, out_off, dp, a, b, false, s_out);
 }
 
 // ---------------------------------------------------------------------------
