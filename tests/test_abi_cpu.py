@@ -64,6 +64,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ir_filter_run(None, None, 1, 1, 1, 0, 3, None) == _lib.IR_EINVAL
     assert lib.ir_filter_run2(None, None, 1, None, 1, 1, 1, 0, 3, None, None) == _lib.IR_EINVAL
     assert lib.ir_filter_run_batch(None, None, 0, None) == _lib.IR_EINVAL
+    assert lib.ir_filter_run_host(None, None, 0, 0, None) == _lib.IR_EINVAL
     assert lib.ir_filter_sync_status(None) == _lib.IR_EINVAL
     assert lib.ir_filter_launch_count(None) == 0
     assert lib.ir_filter_set_border(None, 0) == _lib.IR_EINVAL
