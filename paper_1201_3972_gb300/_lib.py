@@ -321,6 +321,13 @@ class Filter:
         descs = self.make_descs(frames)
         self.ir_filter_run_batch(descs, len(descs), stream)
 
+    def run_host(self, frames, chunks: int = 0, stream=None) -> None:
+        """Frames in host memory: dicts as for ``run_batch`` whose ``in`` and
+        ``out`` are CPU tensors (pinned for full speed); asynchronous on
+        ``stream`` like every other call."""
+        descs = self.make_descs(frames)
+        self.ir_filter_run_host(descs, len(descs), chunks, stream)
+
     def plan(self, frames) -> "BatchPlan":
         descs = self.make_descs(frames)
         return BatchPlan(self, descs)
