@@ -259,3 +259,18 @@ int main() {
             pytest.skip("no host compiler for the layout check: " + r.stderr[-300:])
         n, bad = map(int, subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split())
     assert n > 100 and bad == 0
+
+
+def test_descriptors_from_cpu_tensors():
+    """The binding's descriptors for host frames (run_host) take the host
+    address, geometry, pitch and pixel type of CPU tensors."""
+    import torch
+    a = torch.zeros((7, 40), dtype=torch.int16)
+    b = torch.zeros((7, 48), dtype=torch.int16)[:, :40]        # a row pitch wider than the row
+    c = torch.zeros((3, 5), dtype=torch.uint8)
+    d = _lib.Filter.make_descs([{"in": a, "out": b, "k": 5, "u14": True}, {"in": c, "out": c.clone(), "k": 3}])
+    assert d[0].in_ == a.data_ptr() and d[0].out == b.data_ptr()
+    assert (d[0].H, d[0].W, d[0].in_pitch, d[0].out_pitch, d[0].k) == (7, 40, 80, 96, 5)
+    assert d[0].dtype == _lib.IR_U14 and d[1].dtype == _lib.IR_U8
+    assert (d[1].H, d[1].W, d[1].in_pitch) == (3, 5, 5)
+    assert not d[0].flagged_count
