@@ -9,14 +9,18 @@
  *   - a noisy pixel is replaced by the median g_m of S_xy and every other
  *     pixel is left unchanged (Sec. 3.4).
  * Readings this library fixes where the paper is silent: the border is
- * replicated (every pixel gets a full k x k window), every window reads the
- * unfiltered input (one non-recursive pass), ties with g_min/g_max flag, and
- * k is odd so g_m is the element of rank (k*k-1)/2 of the sorted window.
+ * replicated by default (every pixel gets a full k x k window; mirror and
+ * zero are options), every window reads the unfiltered input (one
+ * non-recursive pass), ties with g_min/g_max flag, and k is odd so g_m is the
+ * element of rank (k*k-1)/2 of the sorted window. A second detector after
+ * Fig. 1 (the line test of ir_filter_set_detector) is an option.
  * Results are integer-exact: every entry point returns the same bytes as a
  * plain CPU evaluation of the rules above.
  *
  * Memory: every frame pointer is a CUDA DEVICE pointer to a row-pitched
- * image (pitch in bytes, rows contiguous). The caller owns all frame memory.
+ * image (pitch in bytes, rows contiguous), except for ir_filter_run_host and
+ * ir_server_submit/read, which take host memory. The caller owns all frame
+ * memory.
  * A handle owns its scratch memory (grown on demand), cached tensor maps,
  * its tuning table and a device status word. Handles are not thread-safe:
  * use one per host thread (several may share a device).
