@@ -65,6 +65,22 @@ def recorded_traffic(k: str, frames: int):
     return int(rec["bytes_per_frame"][k]) * frames
 
 
+def recorded_large_k_profile():
+    """The committed ncu record of the large-window class kernels (ALU-pipe
+    and issue utilisation per k), or None when their sources changed since."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "alu_large_k_1280x1024_u14.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha1()
+    for src in rec["kernel_sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            h.update(fh.read())
+    return rec if h.hexdigest() == rec["kernel_sources_sha1"] else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -137,6 +153,29 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
+def bench_config(replicas: int) -> dict:
+    """The workload as both arms name it (the same dict for the reference arm)."""
+    nframes = 12 * replicas
+    frame_bytes = 640 * 512 * 2
+    return {"workload": WORKLOAD, "frame": "640x512 uint16 14-bit", "frames_per_step": nframes,
+            "replicas": replicas, "mpx_per_step": round(nframes * 640 * 512 / 1e6, 3),
+            "l2": (f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step > 129 MB L2 (no flush needed)"
+                   if nframes * frame_bytes > L2_BYTES else
+                   f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step fit in the 129 MB L2 (small run)")
+            + f"; side legs flush L2 ({2 * L2_BYTES // 10**6} MB write) before each of {LEG_ITERS} timed launches",
+            "parallelism": "frames sharded per GPU, no collective"}
+
+
+# The paper's own timings (Table 1, Sec. 4) with their hardware: context
+# only, a different workload (one 364x244 8-bit image) on other hardware.
+PAPER_CONTEXT = {
+    "source": "Table 1 (Sec. 4): Matlab on an Intel Core 2 E6600 (2.4 GHz, 2 cores), one 364x244 8-bit IR image",
+    "fnr_ms": {"20pct": 15, "30pct": 18}, "mf_ms": 24,
+    "fnr_mpx_s_derived": {"20pct": 5.9, "30pct": 4.9},
+    "sorts": {"20pct": 24587, "30pct": 30832, "of_pixels": 88816},
+}
+
+
 def build_workload(replicas: int):
     from paper_1201_3972_gb300 import synth
     specs = synth.workload_sweep_u14()
@@ -350,63 +389,96 @@ def own_arm(args):
     # dominant kernel = the window class with the largest share of the step
     dom_k = max(per_k, key=lambda kk: per_k[kk]["ms"])
     dom = per_k[dom_k]
+    prof = recorded_profile() or {}
     roofline = {"bound": "hbm", "kernel": f"fnr_kernel k={dom_k} u16 ({_lib.ALGO_NAMES[dom['config']['algo']]})",
                 "achieved": round(dom["achieved_gbs"], 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(dom["achieved_gbs"] / hbm_peak, 4),
                 "traffic": recorded_traffic(dom_k, dom["frames"]),
                 # what does bind it, from the same ncu record (percent of peak)
-                "alu_pipe_pct_ncu": (recorded_profile() or {}).get("alu_pipe_pct", {}).get(dom_k),
-                "issue_active_pct_ncu": (recorded_profile() or {}).get("issue_active_pct", {}).get(dom_k),
-                "peak_kind": f"{peak_kind} copy bandwidth (burst)"}
+                "alu_pipe_pct_ncu": prof.get("alu_pipe_pct", {}).get(dom_k),
+                "issue_active_pct_ncu": prof.get("issue_active_pct", {}).get(dom_k),
+                "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                # every window class of the step, each timed alone (fraction of the same peak)
+                "class_frac": {f"k{k}": round(v["hbm_frac"], 4) for k, v in per_k.items()},
+                "plain_per_frame_mpx_s": round(plain_mpx, 1)}
 
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u16", "data": "synthetic (seeded T^4 thermal field + impulses)",
-        "config": {"workload": WORKLOAD, "frame": "640x512 uint16 14-bit", "frames_per_step": nframes,
-                   "replicas": R, "mpx_per_step": round(step_px / 1e6, 3),
-                   "l2": (f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step > 129 MB L2 (no flush needed)"
-                          if nframes * frame_bytes > L2_BYTES else
-                          f"inputs {nframes * frame_bytes / 1e6:.0f} MB per step fit in the 129 MB L2 (small run)")
-                   + f"; side legs (per_k, directional, batch, large k, single frame) write {2 * L2_BYTES // 10**6} MB"
-                   f" before each of their {LEG_ITERS} timed iterations to flush L2",
-                   "parallelism": f"frames sharded per GPU (dp{world}), no collective"},
+        "config": bench_config(R),
         "roofline": roofline,
-        "per_k": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in v.items()}
-                  for k, v in per_k.items()},
-        "plain_per_frame_mpx_s": round(plain_mpx, 1),
         "e2e": {"value": round(world * step_px / e2e_s / 1e6, 1), "unit": UNIT, "call": "ir_filter_run_host",
                 "chunks": n_chunks, "streams": 3,
                 "readback_equals_device_result": e2e_ok,
                 "h2d_bytes_per_step": nframes * frame_bytes, "d2h_bytes_per_step": nframes * frame_bytes},
         "gpu_launches": int(gpu_launches), "launches_per_step": launches_per_step,
         "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "paper_context": PAPER_CONTEXT,
+        "per_k": {k: {"mpx_s": round(v["mpx_s"], 1), "ms": round(v["ms"], 4), "hbm_frac": round(v["hbm_frac"], 4),
+                      "flagged": round(v["flagged_fraction"], 4), "algo": _lib.ALGO_NAMES[v["config"]["algo"]],
+                      "tile": f"{v['config']['tile_w']}x{v['config']['tile_h']}"}
+                  for k, v in per_k.items()},
     }
     if directional:
         result["directional_detector"] = directional
     if rank == 0:
         result["single_frame"] = single_frame_leg(flt, stream, args)
     if rank == 0 and not args.no_batch_leg:
-        result["batch_mixed"] = batch_leg(flt, stream, args)
+        bm = batch_leg(flt, stream, args)
+        result["batch_mixed"] = bm
+        roofline["batch_k3_k5_frac"] = bm["k3_k5"]["hbm_frac"]
+        roofline["batch_all_frac"] = bm["all"]["hbm_frac"]
     if rank == 0 and not args.no_large_k:
-        result["large_k"] = large_k_leg(flt, stream, args)
+        lk = large_k_leg(flt, stream, args)
+        result["large_k"] = lk
+        # the large windows are bound by integer ALU work: their ALU-pipe
+        # utilisation from the committed ncu record of the same sources
+        lrec = recorded_large_k_profile() or {}
+        roofline["large_k_alu_pipe_pct_ncu"] = lrec.get("alu_pipe_pct")
     if rank == 0 and not args.no_quality:
         from paper_1201_3972_gb300 import quality
-        result["table1_synthetic"] = quality.table1(flt)
-        result["detail_retention"] = quality.detail_retention(flt)
-    if rank == 0 and args.serve_seconds > 0:
-        result["serve"] = serve_leg(args, local)
+        t1 = quality.table1(flt)
+        result["table1_synthetic"] = {key: {"psnr_noisy_mf_fnr": [v["noisy_psnr"], v["mf1_psnr"], v["fnr1_psnr"]],
+                                            "sorts_fnr": v["fnr1_sorts"][0]} for key, v in t1.items()}
+        dr = quality.detail_retention(flt)
+        result["detail_retention"] = {f"k{k}": {"fnr_kept": dr[f"k{k}"]["fnr"]["structure"]["kept"],
+                                                "mf_kept": dr[f"k{k}"]["mf"]["structure"]["kept"]} for k in (3, 5, 7)}
+    ref_hashes = None
     if rank == 0 and not args.no_cpu_baseline:
         plan.launch(stream)  # the output buffer holds the timed step's result, whatever the legs wrote since
         torch.cuda.synchronize()
-        result["cpu_baseline"], result["parity"] = cpu_baseline(frames, specs, d_out, fpx, args)
+        result["cpu_baseline"], result["parity"], ref_hashes = cpu_baseline(frames, specs, d_out, fpx, args)
+    if rank == 0 and args.serve_seconds > 0:
+        result["serve"] = serve_leg(args, local, ref_hashes)
     if rank == 0:
+        result["summary"] = summary(result)
         print(json.dumps(result), flush=True)
     plan.close()
     flt.close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def summary(r: dict) -> dict:
+    """The figures the gates are read from, repeated compactly at the end of
+    the line (HBM fractions of the measured copy bandwidth)."""
+    out = {"value_mpx_s": r["value"], "e2e_mpx_s": r["e2e"]["value"],
+           "class_frac": r["roofline"]["class_frac"],
+           "plain_per_frame_mpx_s": r["roofline"]["plain_per_frame_mpx_s"]}
+    if "batch_mixed" in r:
+        out["batch_k3_k5"] = {"mpx_s": r["batch_mixed"]["k3_k5"]["mpx_s"], "frac": r["batch_mixed"]["k3_k5"]["hbm_frac"],
+                              "target_frac": 0.6}
+        out["batch_all"] = {"mpx_s": r["batch_mixed"]["all"]["mpx_s"], "frac": r["batch_mixed"]["all"]["hbm_frac"]}
+    if "serve" in r:
+        sv = r["serve"]
+        out["serve"] = {"p50_ms": sv["latency_ms"]["p50"], "p99_ms": sv["latency_ms"]["p99"], "mpx_s": sv["mpx_s"],
+                        "seconds": sv["seconds"], "verified": sv["verified"], "mismatches": sv["mismatches"],
+                        "verified_against": sv["verified_against"]}
+    if "parity" in r:
+        out["oracle_parity"] = r["parity"]["bit_exact"]
+    return out
 
 
 def batch_leg(flt, stream, args):
@@ -508,15 +580,20 @@ def large_k_leg(flt, stream, args):
     return out
 
 
-def serve_leg(args, device):
+def serve_leg(args, device, oracle_hashes=None):
     """64 simulated 30 fps streams (320x240 / 640x512 / 1280x1024, 14-bit,
     10% impulses, windows 3/5/7) served by the continuous-batching server:
-    open-loop latency, closed-loop saturation throughput, and the plain
-    one-frame-per-launch path on the same traffic."""
+    open-loop latency with every served output hashed and compared, closed-loop
+    saturation throughput, and the plain one-frame-per-launch path on the same
+    traffic. The expected hashes are the oracle's (from the CPU-baseline leg)
+    when it ran, else those of the plain entry point."""
     from paper_1201_3972_gb300 import serve, synth
     streams = synth.workload_serve(streams=64, pool=args.serve_pool)
     pools = serve.make_pools(streams)
-    ref = serve.reference_hashes(pools, streams, device)
+    if oracle_hashes is not None:
+        ref, against = oracle_hashes, "oracle"
+    else:
+        ref, against = serve.reference_hashes(pools, streams, device), "plain entry point (no oracle run)"
     live = serve.simulate(streams, args.serve_seconds, pools, ref, verify_every=1, device=device)
     sat_s = min(3.0, args.serve_seconds)
     sat = serve.drive(streams, pools, sat_s, inflight=4, device=device)
@@ -525,15 +602,20 @@ def serve_leg(args, device):
             "latency_ms": live["latency_ms"], "mpx_s": live["mpx_s"],
             "frames": live["frames_completed"], "dropped": live["frames_dropped_busy"],
             "mean_batch_frames": live["mean_batch_frames"], "max_inflight_batches": live["max_inflight_batches"],
-            "verified": live["verified"], "mismatches": live["mismatches"],
-            "saturation": sat, "plain_per_frame_saturation": plain,
+            "verified": live["verified"], "mismatches": live["mismatches"], "verified_against": against,
+            "distinct_frames_hashed": len(ref),
+            "saturation_mpx_s": sat["mpx_s"], "saturation_batch_frames": sat["mean_batch_frames"],
+            "plain_per_frame_saturation_mpx_s": plain["mpx_s"],
             "workload": "64 streams x 30 fps Poisson, 320x240/640x512/1280x1024 u14, k 3/5/7, 10% impulses"}
 
 
 def cpu_baseline(frames, specs, d_out, fpx, args):
     """The oracle, as it stands, on all host cores over one replica of the
     12 sweep frames (repeated until about 10 s of CPU work); its outputs
-    also check replica 0 of the GPU result bit for bit."""
+    also check replica 0 of the GPU result bit for bit. Unless serving is
+    skipped, the oracle also filters every distinct frame the serving leg
+    submits (each (resolution, pool frame, window) once, untimed), whose
+    hashes the served outputs are checked against."""
     import oracle
     cores = os.cpu_count() or 1
     gpu = d_out[: len(frames) * fpx].cpu().numpy().view(np.uint16).reshape(len(frames), *frames[0].shape)
@@ -555,7 +637,16 @@ def cpu_baseline(frames, specs, d_out, fpx, args):
             "sample": f"{reps} pass(es) over the 12 distinct 640x512 sweep frames ({px / 1e6:.1f} Mpx), "
                       f"C oracle, row bands over {cores} threads"}
     parity = {"frames_checked": len(frames), "bit_exact": exact == len(frames)}
-    return base, parity
+    hashes = None
+    if args.serve_seconds > 0:
+        from paper_1201_3972_gb300 import serve, synth
+        streams = synth.workload_serve(streams=64, pool=args.serve_pool)
+        hashes = {}
+        for si, k in sorted({(s.size_index, s.k) for s in streams}):
+            pool = streams[[s.size_index for s in streams].index(si)].pool
+            for j, spec in enumerate(synth.serve_pool(si, pool)):
+                hashes[(si, j, k)] = serve.frame_hash(oracle.fnr_mt(spec.make(), k, cores)[0])
+    return base, parity, hashes
 
 
 def reference_arm(args):
@@ -588,9 +679,10 @@ def reference_arm(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frame": "640x512 uint16 14-bit", "frames_per_step": len(frames)},
+        "config": bench_config(args.replicas),
         "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "one pass over the 12 distinct sweep frames per step"},
+                         "sample": "one pass over the 12 distinct sweep frames per step (a bounded sample of the "
+                                   f"{12 * args.replicas}-frame step; Mpx/s over the frames filtered)"},
         "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -604,7 +696,7 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg duration (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving leg duration (0 = skip)")
     ap.add_argument("--no-batch-leg", action="store_true", help="skip the 256-frame mixed batch")
     ap.add_argument("--no-large-k", action="store_true", help="skip the k = 9..21 windows on 1280x1024 frames")
     ap.add_argument("--no-quality", action="store_true", help="skip the Table 1 style PSNR comparison")

@@ -198,16 +198,29 @@ void ir_batch_plan_destroy(ir_batch_plan *plan);
  * e.g. code inside a graph capture or a real-time frame loop, plug-ins whose
  * host application owns all device memory, or pipelines with a fixed memory
  * budget. Same arguments and result as ir_filter_run, with the library's
- * default (untuned) configuration. The input copy is staged in a fixed 8 MiB
+ * default (untuned) strategy and tile per (dtype, k), the table a new handle
+ * starts from. The input copy is staged in a fixed 8 MiB
  * device array inside the library (every GPU that loads the library holds it
  * until exit): a frame needing more than 8 MiB (H rows of W * bytes per pixel,
  * each row rounded up to 16 bytes) is rejected with IR_EINVAL. All calls
  * share that array, so calls that overlap on the GPU race; order them on one
  * stream. The first call on each device does a one-time set-up and should be
- * made before any stream capture. Errors: IR_EINVAL (arguments, size),
- * IR_ECUDA (launch). Device-side wait timeouts are not reported here. */
+ * made before any stream capture. Errors: IR_EINVAL (arguments, size);
+ * IR_EUNSUPPORTED (the current device's index is 64 or more, or no kernel is
+ * built for the window); IR_ECUDA (the one-time set-up or a launch failed).
+ * A bounded device-side wait that gives up is not reported by this call: it
+ * sets a status word that ir_filter_noalloc_status reads. */
 ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pitch_bytes, ir_dtype dtype, int k,
                                 void *cuda_stream);
+
+/* Read and clear the status word of ir_filter_run_noalloc on the current
+ * device, allocating nothing: waits for the device, then IR_ETIMEOUT if a
+ * bounded wait inside one of its kernels gave up since the last read (that
+ * call's frame is then partly unfiltered), IR_ECHECK in a debug build if an
+ * internal check failed, IR_OK otherwise (also when ir_filter_run_noalloc
+ * never ran on this device). IR_ECUDA if the synchronisation or the read
+ * fails. The paper has no counterpart. */
+ir_status ir_filter_noalloc_status(void);
 
 /* Read and clear the handle's device status word (synchronises the device).
  * IR_ETIMEOUT if a bounded wait inside a kernel gave up since the last call;

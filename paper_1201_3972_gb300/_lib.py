@@ -31,7 +31,7 @@ EXPORTED = (
     "ir_batch_plan_create", "ir_batch_plan_launch", "ir_batch_plan_kernel_count", "ir_batch_plan_destroy",
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
-    "ir_filter_run_noalloc", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
+    "ir_filter_run_noalloc", "ir_filter_noalloc_status", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
     "ir_filter_get_border", "ir_filter_set_detector", "ir_filter_get_detector", "ir_filter_set_strict_alignment",
     "ir_filter_run_host",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
@@ -121,6 +121,7 @@ def load(path: Optional[str] = None):
             "ir_filter_last_error": ([vp], ctypes.c_char_p),
             "ir_filter_version": ([], ctypes.c_char_p),
             "ir_filter_run_noalloc": ([vp, i32, i32, sz, i32, i32, vp], i32),
+            "ir_filter_noalloc_status": ([], i32),
             "ir_filter_median_filter": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, vp, vp], i32),
             "ir_filter_set_border": ([vp, i32], i32),
             "ir_filter_get_border": ([vp], i32),

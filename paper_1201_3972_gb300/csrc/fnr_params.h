@@ -90,6 +90,21 @@ constexpr int kPlaneGroup = 4;  // (row, word) items of a bit-plane build step
 __host__ __device__ constexpr bool pool_medians(int algo, int k) { return algo == ALGO_NETWORK && k >= 9; }
 constexpr int kMaxStages = 3;
 
+// Default strategy and output tile per (pixel size, k), used by handles until
+// tuned and by the allocation-free entry point. Measured on GB300 (tile
+// sweeps of all strategies): the 640x512 14-bit sweep for k <= 7; for the
+// bit-plane windows, 1280x1024 frames with sparse random-valued impulses and
+// the mixed batch's dense k = 15 frames, where a taller strip (16 rows per
+// warp) builds fewer halo rows of planes per output row.
+struct DefaultTile {
+  int algo, tile_w, tile_h;
+};
+__host__ __device__ constexpr DefaultTile default_tile(int /*esize: the same for both pixel sizes*/, int k) {
+  return k == 3   ? DefaultTile{ALGO_DENSE3, 128, 64}
+         : k <= 9 ? DefaultTile{ALGO_NETWORK, 64, 64}
+                  : DefaultTile{ALGO_BITPLANE, 32, 128};
+}
+
 // Rows per vertical/horizontal extreme group of the compacted strategies.
 __host__ __device__ constexpr int row_group(int k) { return k >= 8 ? 8 : (k >= 4 ? 4 : 2); }
 

@@ -151,27 +151,12 @@ class DeviceGuard {
 // configuration
 // ---------------------------------------------------------------------------
 static ir_kernel_config default_config(int esize, int k) {
+  const DefaultTile d = default_tile(esize, k);
   ir_kernel_config c{};
   c.ctas_per_sm = 0;
-  // measured on GB300 (tile sweeps of all strategies): the 640x512 14-bit
-  // sweep for k <= 7; for the bit-plane windows, 1280x1024 frames with sparse
-  // random-valued impulses and the mixed batch's dense k = 15 frames, where a
-  // taller strip (16 rows per warp) builds fewer halo rows of planes per
-  // output row
-  if (k == 3) {
-    c.algo = IR_ALGO_DENSE3;
-    c.tile_w = 128;
-    c.tile_h = 64;
-  } else if (k <= 9) {
-    c.algo = IR_ALGO_NETWORK;
-    c.tile_w = 64;
-    c.tile_h = 64;
-  } else {
-    c.algo = IR_ALGO_BITPLANE;
-    c.tile_w = 32;
-    c.tile_h = 128;
-  }
-  (void)esize;
+  c.algo = d.algo;
+  c.tile_w = d.tile_w;
+  c.tile_h = d.tile_h;
   return c;
 }
 

@@ -25,7 +25,10 @@
 //     before any stream capture;
 //   * nothing here calls cudaMalloc, cudaFree or any allocating library
 //     routine; the window configuration is the library's default per (pixel
-//     type, k), not a tuned one.
+//     type, k) (default_tile in fnr_params.h, the table a handle starts
+//     from), not a tuned one;
+//   * a kernel whose bounded wait gave up ORs a flag into a second static
+//     word, which ir_filter_noalloc_status reads and clears.
 #include "ir_filter.h"
 
 #include <cuda.h>
@@ -88,10 +91,12 @@ const void *kernel_for_k(int esize, int k, int algo) {
   return get_kernel_k17_21(esize, k, algo);
 }
 
-void static_config(int k, int &algo, int &tw, int &th) {
-  algo = k == 3 ? ALGO_DENSE3 : (k <= 9 ? ALGO_NETWORK : ALGO_BITPLANE);
-  tw = k == 3 ? 128 : 64;
-  th = 64;
+// The library's default strategy and tile (the table handles start from).
+void static_config(int esize, int k, int &algo, int &tw, int &th) {
+  const DefaultTile d = default_tile(esize, k);
+  algo = d.algo;
+  tw = d.tile_w;
+  th = d.tile_h;
 }
 
 // One-time set-up of `dev` (the current device). Called under g_mu.
@@ -116,7 +121,7 @@ ir_status setup_device(int dev, DeviceState &st) {
   for (int k = 3; k <= kMaxK; k += 2) {
     for (int es = 1; es <= 2; ++es) {
       int algo, tw, th;
-      static_config(k, algo, tw, th);
+      static_config(es, k, algo, tw, th);
       const void *fn = kernel_for_k(es, k, algo);
       if (!fn) continue;
       if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, st.max_smem)) != cudaSuccess)
@@ -166,7 +171,7 @@ extern "C" ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pit
   }
 
   int algo, tw, th;
-  static_config(k, algo, tw, th);
+  static_config(esize, k, algo, tw, th);
   const void *fn = kernel_for_k(esize, k, algo);
   if (!fn) return err(IR_EUNSUPPORTED, "no kernel built for this window");
   const Layout L = make_layout(esize, k, algo, th, tw);
@@ -207,5 +212,31 @@ extern "C" ir_status ir_filter_run_noalloc(void *frame, int H, int W, size_t pit
   void *args[] = {&prm};
   e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, L.total, s);
   if (e != cudaSuccess) return err(IR_ECUDA, "kernel launch failed", e);
+  return IR_OK;
+}
+
+// The status word of the allocation-free path on the current device: its
+// kernels OR a flag into it when a bounded wait gives up (they then leave part
+// of the frame unfiltered). This waits for the device, reads the word into a
+// host variable and clears it; like the entry point it allocates nothing. A
+// device on which ir_filter_run_noalloc never ran has nothing to report.
+extern "C" ir_status ir_filter_noalloc_status(void) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return err(IR_ECUDA, "cudaGetDevice failed", e);
+  if (dev < 0 || dev >= kMaxDevices) return err(IR_EUNSUPPORTED, "device index out of range");
+  unsigned int *status = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_dev[dev].ready) return IR_OK;
+    status = g_dev[dev].status;
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return err(IR_ECUDA, "cudaDeviceSynchronize failed", e);
+  unsigned int word = 0;
+  if ((e = cudaMemcpy(&word, status, sizeof word, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return err(IR_ECUDA, "reading the status word failed", e);
+  if ((e = cudaMemset(status, 0, sizeof word)) != cudaSuccess) return err(IR_ECUDA, "clearing the status word failed", e);
+  if (word & kStatusTimeout) return err(IR_ETIMEOUT, "a bounded device-side wait gave up");
+  if (word & kStatusCheck) return err(IR_ECHECK, "an index or alignment check inside a kernel failed");
   return IR_OK;
 }

@@ -1,7 +1,8 @@
 """GPU tests of the continuous-batching server (ir_server_*).
 
-* each served result equals the same frame filtered alone by the plain entry
-  point (tolerance 0), and the plain path equals the CPU oracle;
+* every served result hashes equal to the CPU oracle's result for its frame
+  (tolerance 0), and so does the same frame filtered alone by the plain entry
+  point, for every pool frame of every (resolution, window) the streams use;
 * 64 streams at 30 fps: p99 latency under 33 ms, nothing dropped or wrong;
 * admission by free HBM, back-pressure and a client that stalls or never
   releases its slots are injected on the host; no GPU fault is involved.
@@ -23,23 +24,32 @@ def pools_and_ref():
     _build.build()
     streams = synth.workload_serve(streams=64, pool=8)
     pools = serve.make_pools(streams)
-    ref = serve.reference_hashes(pools, streams)
-    return streams, pools, ref
+    return streams, pools, oracle_hashes(pools, streams)
+
+
+def oracle_hashes(pools, streams):
+    """The oracle's hash of every (resolution, pool frame, k) the streams use."""
+    out = {}
+    for si, k in sorted({(s.size_index, s.k) for s in streams}):
+        for j, f in enumerate(pools.frames[si]):
+            out[(si, j, k)] = serve.frame_hash(oracle.fnr_mt(f, k, 16)[0])
+    return out
 
 
 def test_plain_reference_matches_oracle(pools_and_ref):
     streams, pools, ref = pools_and_ref
-    # every (resolution, k) of the 64 streams, two pool frames each
-    for si, k in sorted({(s.size_index, s.k) for s in streams}):
-        for j in (0, 5):
-            want, _ = oracle.fnr_mt(pools.frames[si][j], k, 16)
-            assert serve.frame_hash(want) == ref[(si, j, k)]
+    # every (resolution, k) of the 64 streams, every pool frame
+    plain = serve.reference_hashes(pools, streams)
+    assert set(plain) == set(ref) and len(ref) == 9 * 8
+    for key, h in ref.items():
+        assert plain[key] == h, key
 
 
 def test_results_identical_alone_and_in_the_mix(pools_and_ref):
     """Closed loop over 9 streams (3 resolutions x 3 windows) keeps several
     batches in flight; every served output is read back and must hash equal
-    to the same frame filtered alone."""
+    to the oracle's result for its frame (which the same frame filtered alone
+    also equals)."""
     streams, pools, ref = pools_and_ref
     nine = [s for s in streams[:9]]
     res = serve.simulate(nine, 1.5, pools, ref, verify_every=1, closed_loop=True)
@@ -142,15 +152,12 @@ def test_native_drive_saturates_served_and_plain(pools_and_ref):
 
 def test_large_windows_served(pools_and_ref):
     """Streams at k = 9 (pooled network), 15 and 21 (bit planes and the
-    warp-wide radix) through the server: every served output equals the plain
-    path, and the plain path equals the oracle."""
+    warp-wide radix) through the server: every served output hashes equal to
+    the oracle's result for its frame."""
     import dataclasses
     streams, pools, _ = pools_and_ref
     big = [dataclasses.replace(s, k=k, stream_id=i) for i, (s, k) in enumerate(zip(streams[:3], (9, 15, 21)))]
-    ref = serve.reference_hashes(pools, big)
-    for s in big:
-        want, _ = oracle.fnr_mt(pools.frames[s.size_index][0], s.k, 16)
-        assert serve.frame_hash(want) == ref[(s.size_index, 0, s.k)]
+    ref = oracle_hashes(pools, big)
     res = serve.simulate(big, 1.0, pools, ref, verify_every=1, closed_loop=True)
     assert res["frames_completed"] > 10
     assert res["mismatches"] == 0 and res["verified"] == res["frames_completed"]

@@ -5,9 +5,10 @@ real-time loops, plug-ins whose host owns all device memory, fixed-budget
 pipelines): it filters in place through a fixed device array inside the
 library instead of a handle and cudaMalloc'd scratch. This file is named to
 be collected last. Each test compares the new entry point with the existing
-in-place entry point, ir_filter_run, bit for bit (the tolerance of every
-parity test here), on two calls in a row, so contents left in the shared
-array by the first call cannot leak into the second.
+in-place entry point, ir_filter_run, and with the CPU oracle, bit for bit
+(the tolerance of every parity test here), on two calls in a row, so
+contents left in the shared array by the first call cannot leak into the
+second; after the calls, the path's own status word must report no timeout.
 """
 import ctypes
 
@@ -33,8 +34,11 @@ def _host(t, dtype):
 
 def test_noalloc_matches_run_on_two_calls_in_a_row():
     import torch
+
+    import oracle
     from paper_1201_3972_gb300 import _build
     _build.build()
+    oracle.build()
     lib = _lib.load()
     flt = _lib.Filter(0)
     try:
@@ -42,18 +46,24 @@ def test_noalloc_matches_run_on_two_calls_in_a_row():
             (synth.workload_sweep_u14()[4].make(), synth.U14, 5),              # 640x512 14-bit
             (synth.workload_single_u8()[0].make(), synth.U8, 3),               # 320x240 u8
             (synth.make_frame(123, 201, synth.U14, 77, 8.0, 0.3), synth.U14, 9),  # ragged, unaligned rows
+            # the bit-plane strategy of the large windows, both pixel types, odd widths
+            (synth.make_frame(150, 203, synth.U8, 78, 2.0, 0.2), synth.U8, 15),
+            (synth.make_frame(131, 257, synth.U14, 79, 8.0, 0.2, "rv"), synth.U14, 21),
         ]
         stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
         for frame, dt, k in cases:
             H, W = frame.shape
             pitch = W * frame.itemsize
+            want, _ = oracle.fnr(frame, k)
             for _call in range(2):
                 ref = _device_copy(frame)
                 flt.ir_filter_run(int(ref.data_ptr()), H, W, pitch, dt, k)
                 new = _device_copy(frame)
                 st = lib.ir_filter_run_noalloc(ctypes.c_void_p(int(new.data_ptr())), H, W, pitch, dt, k, stream)
                 assert st == _lib.IR_OK
-                np.testing.assert_array_equal(_host(new, frame.dtype), _host(ref, frame.dtype))
+                got = _host(new, frame.dtype)
+                np.testing.assert_array_equal(got, _host(ref, frame.dtype))
+                np.testing.assert_array_equal(got, want)
             # the two calls above ran on different frames too: now swap in a
             # different frame of the same shape to make stale contents visible
             other = frame[::-1].copy()
@@ -63,6 +73,10 @@ def test_noalloc_matches_run_on_two_calls_in_a_row():
             assert lib.ir_filter_run_noalloc(ctypes.c_void_p(int(new.data_ptr())), H, W, pitch, dt, k,
                                              stream) == _lib.IR_OK
             np.testing.assert_array_equal(_host(new, frame.dtype), _host(ref, frame.dtype))
+            np.testing.assert_array_equal(_host(new, frame.dtype), oracle.fnr(other, k)[0])
+        # no bounded wait of the allocation-free kernels gave up, and the read cleared the word
+        assert lib.ir_filter_noalloc_status() == _lib.IR_OK
+        assert lib.ir_filter_noalloc_status() == _lib.IR_OK
         flt.sync_status()
     finally:
         flt.close()
