@@ -66,7 +66,9 @@ typedef enum {
   IR_ALGO_AUTO = 0,          /* tuned choice for (dtype, k) */
   IR_ALGO_DENSE3 = 1,        /* k = 3 only: median for every pixel with shared column sorts, packed 16x2 */
   IR_ALGO_NETWORK = 2,       /* k <= 9: flagged pixels compacted, register selection network each */
-  IR_ALGO_BITPLANE = 3       /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
+  IR_ALGO_BITPLANE = 3,      /* any k: flagged pixels compacted, bit-plane radix select (MSB first) */
+  IR_ALGO_DENSE = 4          /* k = 5 and 7: median for every pixel from separable networks (columns sorted
+                                once for two rows, merges shared by neighbouring windows), packed 16x2 */
 } ir_algo;
 
 /* How windows read pixels outside the frame. The paper does not say; every

@@ -18,13 +18,13 @@ LIB_PATH = os.path.join(PKG, "libirfnr.so")
 
 IR_OK, IR_EINVAL, IR_EALIGN, IR_ENOMEM, IR_ECUDA, IR_ETIMEOUT, IR_EBUSY, IR_EUNSUPPORTED, IR_ECHECK = range(9)
 IR_U8, IR_U16, IR_U14 = 0, 1, 2
-IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE = 0, 1, 2, 3
+IR_ALGO_AUTO, IR_ALGO_DENSE3, IR_ALGO_NETWORK, IR_ALGO_BITPLANE, IR_ALGO_DENSE = 0, 1, 2, 3, 4
 IR_BORDER_REPLICATE, IR_BORDER_MIRROR, IR_BORDER_ZERO = 0, 1, 2
 BORDER_CODES = {"replicate": IR_BORDER_REPLICATE, "mirror": IR_BORDER_MIRROR, "zero": IR_BORDER_ZERO}
 IR_DETECT_EXTREME, IR_DETECT_DIRECTIONAL = 0, 1
 DETECTOR_CODES = {"extreme": IR_DETECT_EXTREME, "directional": IR_DETECT_DIRECTIONAL}
 ALGO_NAMES = {IR_ALGO_AUTO: "auto", IR_ALGO_DENSE3: "dense3", IR_ALGO_NETWORK: "network",
-              IR_ALGO_BITPLANE: "bitplane"}
+              IR_ALGO_BITPLANE: "bitplane", IR_ALGO_DENSE: "dense"}
 
 EXPORTED = (
     "ir_filter_create", "ir_filter_destroy", "ir_filter_run", "ir_filter_run2", "ir_filter_run_batch",

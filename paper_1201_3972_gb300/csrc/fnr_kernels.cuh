@@ -21,6 +21,7 @@
 
 #include "fnr_networks.cuh"
 #include "fnr_params.h"
+#include "fnr_separable.cuh"
 
 namespace fnr {
 
@@ -337,6 +338,12 @@ struct PackedOp {
       b = imad(lo, neg, imad(a, unit, b));
     a = lo;
   }
+  // max(a, b) of an exchange whose min `lo` is computed anyway
+  template <int J>
+  __device__ __forceinline__ uint32_t cmax(uint32_t a, uint32_t b, uint32_t lo) const {
+    if (J % kCxPeriod < kCxAlu) return vmax2(a, b);
+    return imad(lo, neg, imad(a, unit, b));
+  }
 };
 
 __device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
@@ -468,6 +475,126 @@ __device__ void dense3_strip(const T *S, const FrameDev *f, int x0, int y0, int 
       const uint32_t row = ((1u << nlo) - 1u) | (((1u << nhi) - 1u) << 16);
       const uint32_t valid = (ty < th_valid ? row : 0u) | (ty + 1 < th_valid ? row << 4 : 0u);
       flagged += __popc(~dsig & valid);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// DENSE (k = 5, 7): the median of every pixel from the separable networks of
+// fnr_separable.cuh (columns sorted once for two output rows, sorted columns
+// merged into blocks that neighbouring windows share), kept where the
+// detector flags the pixel.
+//
+// A lane item is a pair of output rows times eight output columns. The
+// item's k+1 stage rows are loaded as x-packed words (two neighbouring
+// pixels per word, columns x0 + kFirstCol ..); the network hands back, per
+// output column, row-packed words (low half row y, high half row y+1) of
+// g_m, g_min and g_max; the flag test and the blend run on those, and byte
+// permutes turn the results back into rows for 16-byte (u16) or 8-byte (u8)
+// stores straight to the frame (no output tile).
+// ---------------------------------------------------------------------------
+// x-packed word `WORD` (columns x0 + kFirstCol + 2 WORD and the next) of the
+// item's stage row `ROW`, read where the network first needs it.
+template <typename T, int K>
+struct DenseLoad {
+  const T *base;  // stage row of the item's first row, column x0 + kFirstCol
+  int BW;
+  template <int ROW, int WORD>
+  __device__ __forceinline__ uint32_t get() const {
+    if constexpr (sizeof(T) == 2) {
+      return *reinterpret_cast<const uint32_t *>(base + ROW * BW + 2 * WORD);
+    } else {
+      const uint32_t h = *reinterpret_cast<const uint16_t *>(base + ROW * BW + 2 * WORD);
+      return __byte_perm(h, 0, 0x4140);  // two bytes into two 16-bit halves
+    }
+  }
+};
+
+template <typename T, int K, bool COUNT, int MODE>
+struct DenseEmit {
+  using Net = SepNet<K>;
+  static constexpr int R = (K - 1) / 2;
+  const T *centre;                // stage row of output row y, column x0
+  int BW;
+  const uint32_t (&dsig)[2][4];   // directional detector: x-packed signal bits of rows y, y+1
+  uint32_t (&res)[8];
+  const PackedOp op;
+  const int tx, ty, tw_valid, th_valid;
+  int &flagged;
+  template <int J>
+  __device__ __forceinline__ void put(uint32_t gm, uint32_t gmin, uint32_t gmax) {
+    // the centre pixels of output column x0 + J in rows y and y + 1 (row-packed)
+    uint32_t c;
+    if constexpr (sizeof(T) == 2) {
+      const uint32_t a = *reinterpret_cast<const uint32_t *>(centre + (J & ~1));
+      const uint32_t b = *reinterpret_cast<const uint32_t *>(centre + BW + (J & ~1));
+      c = (J & 1) ? __byte_perm(a, b, 0x7632) : __byte_perm(a, b, 0x5410);
+    } else {
+      c = __byte_perm(static_cast<uint32_t>(centre[J]), static_cast<uint32_t>(centre[BW + J]), 0x7340);
+    }
+    // per 16-bit lane: 1 where the pixel is a signal pixel, 0 where noisy
+    uint32_t sig;
+    if constexpr (MODE == kModeMedian)
+      sig = 0u;
+    else if constexpr (MODE == kModeDirectional)
+      sig = (J & 1) ? __byte_perm(dsig[0][J >> 1], dsig[1][J >> 1], 0x7632)
+                    : __byte_perm(dsig[0][J >> 1], dsig[1][J >> 1], 0x5410);
+    else
+      sig = vmin2(vmin2(op.sub(c, gmin), op.sub(gmax, c)), 0x00010001u);  // g_min <= c <= g_max lane-wise
+    const uint32_t keep = sig * 0xffffu;
+    res[J] = (c & keep) | (gm & ~keep);
+    if constexpr (COUNT) {
+      const uint32_t valid =
+          tx + J < tw_valid ? ((ty < th_valid ? 1u : 0u) | (ty + 1 < th_valid ? 0x10000u : 0u)) : 0u;
+      flagged += __popc((sig ^ 0x00010001u) & valid);
+    }
+  }
+};
+
+template <typename T, int K, bool COUNT, int MODE>
+__device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, int BW, int r0, int SR, int seg_shift,
+                                int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged, const PackedOp op) {
+  using Net = SepNet<K>;
+  constexpr int R = (K - 1) / 2;
+  constexpr int XOFF = xoff_for(R, sizeof(T));
+  static_assert(Net::kRows == K + 1, "network rows");
+  const int items = (SR >> 1) << seg_shift;
+  const int seg_mask = (1 << seg_shift) - 1;
+  unsigned char *const out = f->out;
+  const long long pitch = f->out_pitch;
+  for (int it = lane; it < items; it += 32) {
+    const int sx = it & seg_mask, ry = it >> seg_shift;
+    const int tx = sx << 3, ty = r0 + (ry << 1);
+    const T *const item = S + ty * BW + XOFF + tx;  // stage row ty, output column x0
+    uint32_t dsig[2][4] = {};
+    if constexpr (MODE == kModeDirectional) {
+      // the line test on rows y (stage row ty + R) and y + 1
+      uint32_t e[4][6];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) load_row8<T>(item + (R - 1 + q) * BW, e[q]);
+#pragma unroll
+      for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) dsig[o][pp] = directional_sig(e[o], e[o + 1], e[o + 2], pp, op);
+    }
+    uint32_t res[8];
+    Net::run(op, DenseLoad<T, K>{item + Net::kFirstCol, BW},
+             DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      if (ty + o < th_valid) {
+        uint32_t row[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) row[q] = __byte_perm(res[2 * q], res[2 * q + 1], o ? 0x7632 : 0x5410);
+        T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + tx;
+        if (vec_ok && tx + 8 <= tw_valid) {
+          store_row8<T>(dst, row);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (tx + q < tw_valid) dst[q] = static_cast<T>((row[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+        }
+      }
     }
   }
 }
@@ -1067,8 +1194,18 @@ __device__ __forceinline__ bool debug_tma_ok(int x, int y, int esize, bool store
 
 template <int ALGO, int K>
 struct MinBlocks {
-  // the 81-input network of k = 9 needs about 96 registers
-  static constexpr int value = (ALGO == ALGO_BITPLANE || K >= 9) ? 2 : 3;
+  // the 81-input network of k = 9 needs about 96 registers, as does the dense
+  // 5x5 item; the dense 7x7 item about 150
+  static constexpr int value = ALGO == ALGO_DENSE ? (K >= 7 ? 1 : 2) : ((ALGO == ALGO_BITPLANE || K >= 9) ? 2 : 3);
+};
+
+template <bool B>
+struct Bool {
+  static constexpr bool value = B;
+};
+template <int I>
+struct Int {
+  static constexpr int value = I;
 };
 
 template <typename T, int K, int ALGO>
@@ -1078,6 +1215,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, E);
   static_assert(ALGO != ALGO_DENSE3 || K == 3, "DENSE3 is the 3x3 window only");
+  static_assert(ALGO != ALGO_DENSE || K == 5 || K == 7, "DENSE is built for the 5x5 and 7x7 windows");
 
   const int TW = p.tile_w, TH = p.tile_h;
   const Layout L = make_layout(E, K, ALGO, TH, TW);
@@ -1180,7 +1318,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
 
   // --------------------------------------------------------------- consumers
   const int r0 = warp * SR;  // this warp's output rows [r0, r0 + SR)
-  const int seg_shift = 31 - __clz(TW >> 3);  // dense 3x3: tile_w / 8 is a power of two
+  const int seg_shift = 31 - __clz(TW >> 3);  // dense strategies: tile_w / 8 is a power of two
   const FastDiv divNP(static_cast<uint32_t>(L.np));     // compacted: vertical items per row group
   const FastDiv divG(static_cast<uint32_t>(TW / 8));    // compacted: horizontal items per row
   unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;
@@ -1234,40 +1372,47 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
     T *const S = stage_ptr(s);
     T *const O = (i & 1) ? out1 : out0;  // output tiles alternate independently of the stage ring
 #ifdef FNR_DEBUG_CHECKS
-    if (ALGO != ALGO_DENSE3 && tma_out)
+    if (ALGO != ALGO_DENSE3 && ALGO != ALGO_DENSE && tma_out)
       tma_out = __shfl_sync(0xffffffffu, lane == 0 ? debug_tma_ok(x0, y0 + r0, E, true, O + r0 * TW, p.status) : true,
                             0);
 #endif
     const bool live = y0 + r0 < cur.H;  // any of this strip's rows inside the frame
 
-    if (live && ALGO == ALGO_DENSE3) {
+    if (live && (ALGO == ALGO_DENSE3 || ALGO == ALGO_DENSE)) {
       const PackedOp d3op{p.unit, 0u - p.unit};
+      // the dense 5x5 / 7x7 items read whole words: for odd R one more column
+      // on each side, whose values feed no output
       if (tma_in && p.border != kBorderZero && (x0 < R || ys < 0 || x0 + TW + R > cur.W || ys + BH > cur.H))
         fixup_rows_warp<T>(S, xs, ys, BW, cur.W, cur.H, r0, r0 + SR + K - 1, XOFF - R, XOFF + TW + R - 1, R,
                            p.border, lane);
       // results go straight from registers to the frame (no output tile)
       const bool vec_ok = (cur.flags & kFrameTmaOut) != 0;
       int flagged = 0;
+      auto strip = [&](auto count, auto mode) {
+        if constexpr (ALGO == ALGO_DENSE3)
+          dense3_strip<T, decltype(count)::value, decltype(mode)::value>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift,
+                                                                         cur.W - x0, cur.H - y0, vec_ok, lane,
+                                                                         flagged, d3op);
+        else if constexpr (ALGO == ALGO_DENSE && (K == 5 || K == 7))
+          dense_sep_strip<T, K, decltype(count)::value, decltype(mode)::value>(
+              S, cf, x0, y0, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane, flagged, d3op);
+      };
       if (p.mode == kModeMedian) {
-        dense3_strip<T, false, kModeMedian>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
-                                            lane, flagged, d3op);
+        strip(Bool<false>{}, Int<kModeMedian>{});
         if (cur.counted && lane == 0) {  // every in-frame pixel of the strip takes a median
           const int rows = min(SR, cur.H - y0 - r0), cols = min(TW, cur.W - x0);
           atomicAdd(cf->flagged, static_cast<unsigned long long>(rows) * static_cast<unsigned long long>(cols));
         }
       } else if (p.mode == kModeDirectional) {
-        dense3_strip<T, true, kModeDirectional>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0,
-                                                vec_ok, lane, flagged, d3op);
+        strip(Bool<true>{}, Int<kModeDirectional>{});
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if (cur.counted && lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else if (cur.counted) {
-        dense3_strip<T, true, kModeFnr>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
-                                        lane, flagged, d3op);
+        strip(Bool<true>{}, Int<kModeFnr>{});
         flagged = __reduce_add_sync(0xffffffffu, flagged);
         if (lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       } else {
-        dense3_strip<T, false, kModeFnr>(S, cf, x0, y0, TW, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok,
-                                         lane, flagged, d3op);
+        strip(Bool<false>{}, Int<kModeFnr>{});
       }
     } else if constexpr (ALGO == ALGO_NETWORK && PoolMedians<K>::value) {
       // Every consumer warp takes part, live strip or not: the strips' flagged
@@ -1365,7 +1510,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
         bulk_commit();
         if (flagged != 0 && cur.counted) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
       }
-    } else if (ALGO != ALGO_DENSE3 && lane == 0) {
+    } else if (ALGO != ALGO_DENSE3 && ALGO != ALGO_DENSE && lane == 0) {
       bulk_commit();  // keep one bulk group per tile so the wait above stays exact
     }
     fence_proxy_async_smem();  // this warp's generic writes to the stage precede its refill by TMA
@@ -1383,6 +1528,9 @@ inline const void *kernel_for(int algo) {
       return nullptr;
     case ALGO_NETWORK:
       if constexpr (K <= 9) return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_NETWORK>);
+      return nullptr;
+    case ALGO_DENSE:
+      if constexpr (K == 5 || K == 7) return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_DENSE>);
       return nullptr;
     case ALGO_BITPLANE:
       return reinterpret_cast<const void *>(&fnr_kernel<T, K, ALGO_BITPLANE>);

@@ -13,7 +13,11 @@ constexpr int kMaxK = 21;              // largest window built
 constexpr int kNumK = (kMaxK - 3) / 2 + 1;
 constexpr int kDirMax = 512;           // frames whose tile ranges a CTA keeps in shared memory
 
-enum Algo : int { ALGO_AUTO = 0, ALGO_DENSE3 = 1, ALGO_NETWORK = 2, ALGO_BITPLANE = 3 };
+enum Algo : int { ALGO_AUTO = 0, ALGO_DENSE3 = 1, ALGO_NETWORK = 2, ALGO_BITPLANE = 3, ALGO_DENSE = 4 };
+
+// The dense strategies take a median for every pixel and write results
+// straight from registers: no output tile, no per-warp lists.
+__host__ __device__ constexpr bool dense_algo(int algo) { return algo == ALGO_DENSE3 || algo == ALGO_DENSE; }
 
 // Frame flags
 constexpr int kFrameTmaIn = 1;     // load tiles with TMA (16 B aligned base and pitch)
@@ -81,7 +85,7 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
 
 // Staging buffers per CTA (a ring: the producer loads up to this many tiles
 // ahead of the slowest consumer warp).
-__host__ __device__ constexpr int num_stages(int algo) { return algo == ALGO_DENSE3 ? 3 : 2; }
+__host__ __device__ constexpr int num_stages(int algo) { return dense_algo(algo) ? 3 : 2; }
 __host__ __device__ constexpr int out_buffers(int algo) { return algo == ALGO_BITPLANE ? 1 : 2; }
 constexpr int kPlaneGroup = 4;  // (row, word) items of a bit-plane build step
 // Whether the network strategy pools the flagged pixels of a tile across its
@@ -111,7 +115,7 @@ __host__ __device__ constexpr int row_group(int k) { return k >= 8 ? 8 : (k >= 4
 // tile_h must split into kConsumerWarps strips, each a whole number of row
 // groups (compacted strategies) or of row pairs (dense 3x3).
 __host__ __device__ constexpr int tile_h_multiple(int k, int algo) {
-  return kConsumerWarps * (algo == ALGO_DENSE3 ? 2 : row_group(k));
+  return kConsumerWarps * (dense_algo(algo) ? 2 : row_group(k));
 }
 
 // Shared-memory layout of one CTA (byte offsets). Identical on host and device.
@@ -162,8 +166,8 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   int off = 0;
   // +16: a pair word may read one pixel past the last staged column (never used)
   const int stage = align_up(L.bw * L.bh * esize + 16, 128);
-  // the dense 3x3 strategy writes results straight from registers: no output tile
-  const int outb = algo == ALGO_DENSE3 ? 0 : align_up(tile_w * tile_h * esize, 128);
+  // the dense strategies write results straight from registers: no output tile
+  const int outb = dense_algo(algo) ? 0 : align_up(tile_w * tile_h * esize, 128);
   for (int i = 0; i < kMaxStages; ++i) {
     L.off_stage[i] = off;
     if (i < num_stages(algo)) off += stage;
@@ -179,7 +183,7 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   }
   L.w_list = L.w_vmin = L.w_vmax = L.w_planes = L.w_stage = -1;
   int w = 0;
-  if (algo != ALGO_DENSE3) {
+  if (!dense_algo(algo)) {
     L.list_bytes = align_up(L.sr * tile_w * 2, 16);
     L.w_list = w; w += L.list_bytes * (pool_medians(algo, k) ? 2 : 1);
     L.w_vmin = w; w += align_up(L.sr * L.nps * 4, 16);

@@ -170,11 +170,14 @@ static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_conf
   // halo) and every box row must be a whole number of 16-byte units
   if ((c.tile_w * esize) % 16) return no("tile_w * bytes per pixel must be a multiple of 16");
   if (c.algo == IR_ALGO_DENSE3 && k != 3) return no("DENSE3 is the 3x3 window only");
+  if (c.algo == IR_ALGO_DENSE && k != 5 && k != 7) return no("DENSE is built for k = 5 and 7");
   if (c.algo == IR_ALGO_NETWORK && k > 9) return no("NETWORK is built for k <= 9");
-  if (c.algo != IR_ALGO_DENSE3 && c.algo != IR_ALGO_NETWORK && c.algo != IR_ALGO_BITPLANE) return no("unknown algo");
+  if (c.algo != IR_ALGO_DENSE3 && c.algo != IR_ALGO_NETWORK && c.algo != IR_ALGO_BITPLANE && c.algo != IR_ALGO_DENSE)
+    return no("unknown algo");
   if (c.ctas_per_sm < 0) return no("ctas_per_sm < 0");
   if (c.tile_h % tile_h_multiple(k, c.algo)) return no("tile_h must split into 8 warp strips of whole row groups");
-  if (c.algo == IR_ALGO_DENSE3 && ((c.tile_w / 8) & (c.tile_w / 8 - 1))) return no("DENSE3 needs tile_w / 8 a power of two");
+  if ((c.algo == IR_ALGO_DENSE3 || c.algo == IR_ALGO_DENSE) && ((c.tile_w / 8) & (c.tile_w / 8 - 1)))
+    return no("the dense strategies need tile_w / 8 a power of two");
   const Layout L = make_layout(esize, k, c.algo, c.tile_h, c.tile_w);
   if (L.bw > 256 || L.bh > 256) return no("tile plus halo exceeds the 256-pixel TMA box");
   if (c.tile_w > 256 || c.tile_h > 256) return no("tile side > 256");
@@ -948,6 +951,8 @@ static std::vector<ir_kernel_config> candidates(int esize, int k) {
   } else if (k <= 7) {
     for (int tw : {32, 64, 128})
       for (int th : {32, 64, 128}) add(IR_ALGO_NETWORK, tw, th);
+    for (int tw : {64, 128})
+      for (int th : {32, 64, 128}) add(IR_ALGO_DENSE, tw, th);
     add(IR_ALGO_BITPLANE, 64, 64);
   } else {
     for (int tw : {32, 64, 128})

@@ -26,14 +26,14 @@ from paper_1201_3972_gb300 import _lib, synth  # noqa: E402
 
 def algos_for(k):
     return [_lib.IR_ALGO_BITPLANE] + ([_lib.IR_ALGO_NETWORK] if k <= 9 else []) + \
-        ([_lib.IR_ALGO_DENSE3] if k == 3 else [])
+        ([_lib.IR_ALGO_DENSE3] if k == 3 else []) + ([_lib.IR_ALGO_DENSE] if k in (5, 7) else [])
 
 
 def tiles_for(es, k, algo):
     r = (k - 1) // 2
     xoff = -(-r // (16 // es)) * (16 // es)
     rg = 8 if k >= 8 else (4 if k >= 4 else 2)
-    mult = 8 * (2 if algo == _lib.IR_ALGO_DENSE3 else rg)
+    mult = 8 * (2 if algo in (_lib.IR_ALGO_DENSE3, _lib.IR_ALGO_DENSE) else rg)
     return [(tw, th) for tw, th in ((64, 64), (32, 16), (128, 32), (32, 128))
             if tw + 2 * xoff <= 256 and th + 2 * r <= 256 and (tw * es) % 16 == 0 and th % mult == 0]
 

@@ -203,8 +203,9 @@ int main() {
   int bad = 0, n = 0;
   for (int es = 1; es <= 2; ++es)
     for (int k = 3; k <= kMaxK; k += 2)
-      for (int algo = ALGO_DENSE3; algo <= ALGO_BITPLANE; ++algo) {
+      for (int algo = ALGO_DENSE3; algo <= ALGO_DENSE; ++algo) {
         if (algo == ALGO_DENSE3 && k != 3) continue;
+        if (algo == ALGO_DENSE && k != 5 && k != 7) continue;
         if (algo == ALGO_NETWORK && k > 9) continue;
         for (int tw = 8; tw <= 256; tw += 8)
           for (int th = 8; th <= 256; th += 8) {
@@ -215,7 +216,7 @@ int main() {
             long r[20][2]; int m = 0;
             const long stage = L.off_stage[1] - L.off_stage[0];
             for (int s = 0; s < num_stages(algo); ++s) { r[m][0] = L.off_stage[0] + s * stage; r[m][1] = r[m][0] + (long)L.bw * L.bh * es; ++m; }
-            const long outb = algo == ALGO_DENSE3 ? 0 : (long)tw * th * es;
+            const long outb = dense_algo(algo) ? 0 : (long)tw * th * es;
             for (int o = 0; o < out_buffers(algo); ++o) { r[m][0] = L.off_out[o]; r[m][1] = r[m][0] + outb; ++m; }
             if (out_buffers(algo) == 1 && L.off_out[1] != L.off_out[0]) ++bad;
             r[m][0] = L.off_warp; r[m][1] = L.off_warp + (long)kConsumerWarps * L.warp_bytes; ++m;
@@ -228,7 +229,7 @@ int main() {
               for (int j = i + 1; j < m; ++j)
                 if (r[i][1] > r[i][0] && r[j][1] > r[j][0] && overlap(r[i][0], r[i][1], r[j][0], r[j][1])) ++bad;
             }
-            if (algo != ALGO_DENSE3) {  // inside a warp block: list, then extremes (planes overlay them)
+            if (!dense_algo(algo)) {  // inside a warp block: list, then extremes (planes overlay them)
               const long list1 = L.w_list + (long)L.list_bytes * (pool_medians(algo, k) ? 2 : 1);
               const long v0 = L.w_vmin, v1 = L.w_vmax + (long)L.sr * L.nps * 4;
               if (L.list_bytes < (long)L.sr * tw * 2) ++bad;

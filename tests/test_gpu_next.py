@@ -29,6 +29,8 @@ def _algos(k):
         out.append(_lib.IR_ALGO_NETWORK)
     if k == 3:
         out.append(_lib.IR_ALGO_DENSE3)
+    if k in (5, 7):
+        out.append(_lib.IR_ALGO_DENSE)
     return out
 
 

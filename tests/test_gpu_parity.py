@@ -36,7 +36,12 @@ def algos_for(k):
         out.append(_lib.IR_ALGO_NETWORK)
     if k == 3:
         out.append(_lib.IR_ALGO_DENSE3)
+    if k in (5, 7):
+        out.append(_lib.IR_ALGO_DENSE)
     return out
+
+
+DENSE_ALGOS = (_lib.IR_ALGO_DENSE3, _lib.IR_ALGO_DENSE)
 
 
 def row_group(k):
@@ -46,10 +51,10 @@ def row_group(k):
 def tiles_for(es, k, algo):
     """Tile shapes the kernels accept: tile_w * bytes a multiple of 16, tile
     plus halo within the 256-pixel TMA box, tile_h split into 8 warp strips
-    of whole row groups (row pairs for the dense 3x3 path)."""
+    of whole row groups (row pairs for the dense paths)."""
     r = (k - 1) // 2
     xoff = -(-r // (16 // es)) * (16 // es)
-    mult = 8 * (2 if algo == _lib.IR_ALGO_DENSE3 else row_group(k))
+    mult = 8 * (2 if algo in DENSE_ALGOS else row_group(k))
     out = []
     for tw, th in ((64, 64), (128, 32), (32, 16), (16, 16), (8, 16), (128, 64), (192, 32), (64, 128)):
         if tw + 2 * xoff <= 256 and th + 2 * r <= 256 and (tw * es) % 16 == 0 and th % mult == 0:
@@ -239,7 +244,7 @@ def test_workload_small_k_full_size(flt, spec):
     f = spec.make()
     want, wf = oracle.fnr(f, spec.k)
     for algo in algos_for(spec.k):
-        flt.set_config(spec.dtype, spec.k, 64 if algo != _lib.IR_ALGO_DENSE3 else 128, 64, algo)
+        flt.set_config(spec.dtype, spec.k, 128 if algo in DENSE_ALGOS else 64, 64, algo)
         got, gf = gpu_fnr(flt, f, spec.k, u14=spec.dtype == _lib.IR_U14)
         np.testing.assert_array_equal(got, want)
         assert gf == wf
