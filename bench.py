@@ -256,6 +256,8 @@ def own_arm(args):
         return arr
 
     all_idx = list(range(nframes))
+    # the autotuner picks each class's strategy and tile on these frames
+    tuned = {str(r["k"]): r for r in flt.autotune_batch(descs_for(all_idx), reps=20, stream=stream)}
     plan = _lib.BatchPlan(flt, descs_for(all_idx))
     launches_per_step = plan.kernel_count
     step_px = nframes * fpx
@@ -400,7 +402,9 @@ def own_arm(args):
                 "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                 # every window class of the step, each timed alone (fraction of the same peak)
                 "class_frac": {f"k{k}": round(v["hbm_frac"], 4) for k, v in per_k.items()},
-                "plain_per_frame_mpx_s": round(plain_mpx, 1)}
+                "plain_per_frame_mpx_s": round(plain_mpx, 1),
+                # the tuner's choice per class and its margin over the default configuration
+                "tuned": {f"k{k}": tune_summary(r) for k, r in tuned.items()}}
 
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -461,6 +465,15 @@ def own_arm(args):
         dist.destroy_process_group()
 
 
+def tune_summary(r: dict) -> dict:
+    from paper_1201_3972_gb300 import _lib
+    c, d = r["chosen"], r["defaults"]
+    return {"algo": _lib.ALGO_NAMES[c["algo"]], "tile": f"{c['tile_w']}x{c['tile_h']}",
+            "default": f"{_lib.ALGO_NAMES[d['algo']]} {d['tile_w']}x{d['tile_h']}",
+            "speedup_vs_default": round(r["default_ms"] / r["chosen_ms"], 3) if r["chosen_ms"] > 0 else None,
+            "candidates": r["candidates"]}
+
+
 def summary(r: dict) -> dict:
     """The figures the gates are read from, repeated compactly at the end of
     the line (HBM fractions of the measured copy bandwidth)."""
@@ -494,6 +507,10 @@ def batch_leg(flt, stream, args):
         src = torch.from_numpy(f.view(np.int16) if f.dtype == np.uint16 else f).cuda()
         bufs.append((src, torch.empty_like(src)))
     out = {}
+    every = flt.make_descs([{"in": bufs[i][0], "out": bufs[i][1], "k": s.k, "u14": s.dtype == synth.U14}
+                            for i, s in enumerate(specs)])
+    tuned = flt.autotune_batch(every, reps=20, stream=stream)
+    out["tuned"] = {f"{'u8' if r['dtype'] == _lib.IR_U8 else 'u16'} k{r['k']}": tune_summary(r) for r in tuned}
     for name, sel in (("all", lambda s: True), ("k3_k5", lambda s: s.k in (3, 5))):
         idx = [i for i, s in enumerate(specs) if sel(s)]
         plan = flt.plan([{"in": bufs[i][0], "out": bufs[i][1], "k": specs[i].k, "u14": specs[i].dtype == synth.U14}
@@ -567,6 +584,7 @@ def large_k_leg(flt, stream, args):
             arr[j].dtype = _lib.IR_U14
             arr[j].k = s.k
             arr[j].flagged_count = None
+        tr = flt.autotune_batch(arr, reps=20, stream=stream)[0]
         plan = _lib.BatchPlan(flt, arr)
         for _ in range(args.warmup):
             plan.launch(stream)
@@ -574,8 +592,7 @@ def large_k_leg(flt, stream, args):
                                            flush=True))
         px = copies * H * W
         out[str(s.k)] = {"frames": copies, "ms": round(ms, 4), "mpx_s": round(px / ms / 1e3, 1),
-                         "hbm_frac": round(px * 4 / (ms * 1e-3) / 1e9 / hbm, 4),
-                         "config": flt.get_config(_lib.IR_U14, s.k)}
+                         "hbm_frac": round(px * 4 / (ms * 1e-3) / 1e9 / hbm, 4), "tuned": tune_summary(tr)}
         plan.close()
     return out
 

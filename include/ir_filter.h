@@ -256,10 +256,42 @@ ir_status ir_filter_set_detector(ir_filter *h, ir_detector detector);
 ir_detector ir_filter_get_detector(const ir_filter *h);
 
 /* Tuning. ir_filter_autotune times every built candidate for (dtype, k) on a
- * synthetic H x W frame on `cuda_stream` and keeps the fastest; the table is
- * per handle. get/set read or override one entry. */
+ * synthetic H x W frame (smooth ramp, 10% salt-and-pepper) on `cuda_stream`,
+ * 20 launches each with L2 flushed before every launch, and keeps the fastest
+ * by median time; synchronous. The table is per handle. get/set read or
+ * override one entry. ir_filter_autotune_batch below tunes on real frames. */
 ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, void *cuda_stream);
 ir_status ir_filter_get_config(ir_filter *h, ir_dtype dtype, int k, ir_kernel_config *out);
+
+/* One (pixel size, k) class tuned by ir_filter_autotune_batch. */
+typedef struct {
+  int dtype;                  /* IR_U8 or IR_U16 (the pixel size; IR_U14 shares IR_U16's entry) */
+  int k;
+  int frames;                 /* frames of the batch in this class */
+  int candidates;             /* configurations timed */
+  ir_kernel_config chosen;    /* the fastest, now the handle's entry for the class */
+  float chosen_ms;            /* median time of one launch of the class's frames with it */
+  ir_kernel_config defaults;  /* the library's default configuration for the class */
+  float default_ms;           /* its median time, measured the same way */
+} ir_tune_result;
+
+/* Tune the handle's table on the caller's own frames: for every (pixel size,
+ * k) class present in descs (the same descriptors as ir_filter_run_batch),
+ * time every built (strategy, tile) candidate, default included, on a batch
+ * plan of exactly that class's frames: `reps` timed launches each (at least
+ * 20; 0 = 20) after two warm-up launches, CUDA events on cuda_stream, with L2
+ * flushed before every timed launch (a device memset over twice the L2 size,
+ * in memory allocated for the call and freed before it returns) unless the
+ * class's frames are larger than that already; the fastest by median time
+ * becomes the handle's entry. The frames are filtered as a side effect (the
+ * outputs hold the filtered frames afterwards; flagged counters are not
+ * touched). Synchronous: returns when tuning is done. results (nullable):
+ * up to max_results entries, one per class, *n_results (nullable) set to the
+ * number of classes. Errors: as ir_batch_plan_create; IR_ENOMEM if the flush
+ * buffer cannot be allocated. The table can then be saved and reused by
+ * later handles on the same GPU model (ir_filter_get_config / set_config). */
+ir_status ir_filter_autotune_batch(ir_filter *h, const ir_frame_desc *descs, int n, int reps, void *cuda_stream,
+                                   ir_tune_result *results, int max_results, int *n_results);
 ir_status ir_filter_set_config(ir_filter *h, ir_dtype dtype, int k, const ir_kernel_config *cfg);
 
 /* Number of FNR kernel launches this handle has issued (graph replays count

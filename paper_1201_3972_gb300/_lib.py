@@ -33,7 +33,7 @@ EXPORTED = (
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
     "ir_filter_run_noalloc", "ir_filter_noalloc_status", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
     "ir_filter_get_border", "ir_filter_set_detector", "ir_filter_get_detector", "ir_filter_set_strict_alignment",
-    "ir_filter_run_host",
+    "ir_filter_run_host", "ir_filter_autotune_batch",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
     "ir_server_release", "ir_server_get_stats", "ir_server_clock", "ir_server_drive",
@@ -55,6 +55,12 @@ class ir_frame_desc(ctypes.Structure):
     _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
                 ("in_pitch", ctypes.c_size_t), ("out_pitch", ctypes.c_size_t), ("dtype", ctypes.c_int),
                 ("k", ctypes.c_int), ("flagged_count", ctypes.c_void_p)]
+
+
+class ir_tune_result(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("k", ctypes.c_int), ("frames", ctypes.c_int), ("candidates", ctypes.c_int),
+                ("chosen", ir_kernel_config), ("chosen_ms", ctypes.c_float), ("defaults", ir_kernel_config),
+                ("default_ms", ctypes.c_float)]
 
 
 class ir_server_config(ctypes.Structure):
@@ -114,6 +120,8 @@ def load(path: Optional[str] = None):
             "ir_batch_plan_destroy": ([vp], None),
             "ir_filter_sync_status": ([vp], i32),
             "ir_filter_autotune": ([vp, i32, i32, i32, i32, vp], i32),
+            "ir_filter_autotune_batch": ([vp, ctypes.POINTER(ir_frame_desc), i32, i32, vp,
+                                          ctypes.POINTER(ir_tune_result), i32, ctypes.POINTER(i32)], i32),
             "ir_filter_get_config": ([vp, i32, i32, ctypes.POINTER(ir_kernel_config)], i32),
             "ir_filter_set_config": ([vp, i32, i32, ctypes.POINTER(ir_kernel_config)], i32),
             "ir_filter_launch_count": ([vp], ctypes.c_ulonglong),
@@ -345,6 +353,22 @@ class Filter:
 
     def autotune(self, dtype: int, k: int, H: int, W: int, stream=None) -> None:
         _check(self.lib, self.h, self.lib.ir_filter_autotune(self.h, dtype, k, H, W, _stream(stream)))
+
+    def autotune_batch(self, descs, reps: int = 20, stream=None) -> list:
+        """Tune the table on these frames (an ``ir_frame_desc`` array, e.g. from
+        ``make_descs``), class by class; returns one dict per (pixel size, k)
+        class: the configuration chosen, its median ms, the default's, and the
+        number of candidates timed."""
+        out = (ir_tune_result * 64)()
+        got = ctypes.c_int(0)
+        _check(self.lib, self.h, self.lib.ir_filter_autotune_batch(self.h, descs, len(descs), int(reps),
+                                                                   _stream(stream), out, 64, ctypes.byref(got)))
+
+        def cfg(c):
+            return {"tile_w": c.tile_w, "tile_h": c.tile_h, "algo": c.algo, "ctas_per_sm": c.ctas_per_sm}
+        return [{"dtype": r.dtype, "k": r.k, "frames": r.frames, "candidates": r.candidates,
+                 "chosen": cfg(r.chosen), "chosen_ms": float(r.chosen_ms), "defaults": cfg(r.defaults),
+                 "default_ms": float(r.default_ms)} for r in out[:got.value]]
 
     def get_config(self, dtype: int, k: int) -> dict:
         c = ir_kernel_config()

@@ -346,6 +346,24 @@ struct PackedOp {
   }
 };
 
+#ifndef FNR_DENSE_CX_PERIOD
+#define FNR_DENSE_CX_PERIOD 8
+#endif
+#ifndef FNR_DENSE_CX_ALU
+#define FNR_DENSE_CX_ALU 1
+#endif
+
+// The separable networks of the dense 5x5 / 7x7 strategy issue little but
+// min/max, so the ALU pipe alone bounds them: all but one in
+// FNR_DENSE_CX_PERIOD of their exchanges take the max on the FMA pipe.
+struct DenseOp : PackedOp {
+  template <int J>
+  __device__ __forceinline__ uint32_t cmax(uint32_t a, uint32_t b, uint32_t lo) const {
+    if (J % FNR_DENSE_CX_PERIOD < FNR_DENSE_CX_ALU) return vmax2(a, b);
+    return imad(lo, neg, imad(a, unit, b));
+  }
+};
+
 __device__ __forceinline__ uint32_t med3v(uint32_t a, uint32_t b, uint32_t c) {
   return vmax2(vmin2(a, b), vmin2(vmax2(a, b), c));
 }
@@ -516,8 +534,8 @@ struct DenseEmit {
   static constexpr int R = (K - 1) / 2;
   const T *centre;                // stage row of output row y, column x0
   int BW;
-  const uint32_t (&dsig)[2][4];   // directional detector: x-packed signal bits of rows y, y+1
-  uint32_t (&res)[8];
+  const uint32_t (&dsig)[2][Net::kOut / 2];  // directional detector: x-packed signal bits of rows y, y+1
+  uint32_t (&res)[Net::kOut];
   const PackedOp op;
   const int tx, ty, tw_valid, th_valid;
   int &flagged;
@@ -530,7 +548,7 @@ struct DenseEmit {
       const uint32_t b = *reinterpret_cast<const uint32_t *>(centre + BW + (J & ~1));
       c = (J & 1) ? __byte_perm(a, b, 0x7632) : __byte_perm(a, b, 0x5410);
     } else {
-      c = __byte_perm(static_cast<uint32_t>(centre[J]), static_cast<uint32_t>(centre[BW + J]), 0x7340);
+      c = __byte_perm(static_cast<uint32_t>(centre[J]), static_cast<uint32_t>(centre[BW + J]), 0x5410);
     }
     // per 16-bit lane: 1 where the pixel is a signal pixel, 0 where noisy
     uint32_t sig;
@@ -557,42 +575,52 @@ __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, i
   using Net = SepNet<K>;
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
-  static_assert(Net::kRows == K + 1, "network rows");
+  constexpr int NO = Net::kOut;  // output columns per item (a multiple of 8)
+  static_assert(Net::kRows == K + 1 && NO % 8 == 0 && NO == dense_item_cols(ALGO_DENSE, K), "network shape");
+  // items: (row pair, NO-column segment); seg_shift = log2(tile_w / NO)
   const int items = (SR >> 1) << seg_shift;
   const int seg_mask = (1 << seg_shift) - 1;
   unsigned char *const out = f->out;
   const long long pitch = f->out_pitch;
   for (int it = lane; it < items; it += 32) {
     const int sx = it & seg_mask, ry = it >> seg_shift;
-    const int tx = sx << 3, ty = r0 + (ry << 1);
+    const int tx = sx * NO, ty = r0 + (ry << 1);
     const T *const item = S + ty * BW + XOFF + tx;  // stage row ty, output column x0
-    uint32_t dsig[2][4] = {};
+    uint32_t dsig[2][NO / 2] = {};
     if constexpr (MODE == kModeDirectional) {
-      // the line test on rows y (stage row ty + R) and y + 1
-      uint32_t e[4][6];
+      // the line test on rows y (stage row ty + R) and y + 1, eight columns at a time
 #pragma unroll
-      for (int q = 0; q < 4; ++q) load_row8<T>(item + (R - 1 + q) * BW, e[q]);
+      for (int g = 0; g < NO / 8; ++g) {
+        uint32_t e[4][6];
 #pragma unroll
-      for (int o = 0; o < 2; ++o)
+        for (int q = 0; q < 4; ++q) load_row8<T>(item + (R - 1 + q) * BW + 8 * g, e[q]);
 #pragma unroll
-        for (int pp = 0; pp < 4; ++pp) dsig[o][pp] = directional_sig(e[o], e[o + 1], e[o + 2], pp, op);
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int pp = 0; pp < 4; ++pp) dsig[o][4 * g + pp] = directional_sig(e[o], e[o + 1], e[o + 2], pp, op);
+      }
     }
-    uint32_t res[8];
-    Net::run(op, DenseLoad<T, K>{item + Net::kFirstCol, BW},
+    uint32_t res[NO];
+    Net::run(DenseOp{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
              DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (ty + o < th_valid) {
-        uint32_t row[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) row[q] = __byte_perm(res[2 * q], res[2 * q + 1], o ? 0x7632 : 0x5410);
-        T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + tx;
-        if (vec_ok && tx + 8 <= tw_valid) {
-          store_row8<T>(dst, row);
-        } else {
+        for (int g = 0; g < NO / 8; ++g) {
+          uint32_t row[4];
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (tx + q < tw_valid) dst[q] = static_cast<T>((row[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+          for (int q = 0; q < 4; ++q)
+            row[q] = __byte_perm(res[8 * g + 2 * q], res[8 * g + 2 * q + 1], o ? 0x7632 : 0x5410);
+          const int cx = tx + 8 * g;
+          T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + cx;
+          if (vec_ok && cx + 8 <= tw_valid) {
+            store_row8<T>(dst, row);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (cx + q < tw_valid) dst[q] = static_cast<T>((row[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+          }
         }
       }
     }
@@ -1318,7 +1346,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
 
   // --------------------------------------------------------------- consumers
   const int r0 = warp * SR;  // this warp's output rows [r0, r0 + SR)
-  const int seg_shift = 31 - __clz(TW >> 3);  // dense strategies: tile_w / 8 is a power of two
+  // dense strategies: items of 8 (3x3) or SepNet<K>::kOut output columns, tile_w / that a power of two
+  const int seg_shift = 31 - __clz(TW / dense_item_cols(ALGO, K));
   const FastDiv divNP(static_cast<uint32_t>(L.np));     // compacted: vertical items per row group
   const FastDiv divG(static_cast<uint32_t>(TW / 8));    // compacted: horizontal items per row
   unsigned char *const wbase = smem + L.off_warp + warp * L.warp_bytes;

@@ -19,6 +19,14 @@ enum Algo : int { ALGO_AUTO = 0, ALGO_DENSE3 = 1, ALGO_NETWORK = 2, ALGO_BITPLAN
 // straight from registers: no output tile, no per-warp lists.
 __host__ __device__ constexpr bool dense_algo(int algo) { return algo == ALGO_DENSE3 || algo == ALGO_DENSE; }
 
+// Output columns of one lane item of the dense strategies (a row pair times
+// this many columns): 8 for the 3x3 path; for the separable networks the
+// generator's choice (fnr_separable.cuh, SepNet<K>::kOut), repeated here for
+// the host's tile checks.
+__host__ __device__ constexpr int dense_item_cols(int algo, int k) {
+  return algo == ALGO_DENSE && k == 7 ? 8 : 8;
+}
+
 // Frame flags
 constexpr int kFrameTmaIn = 1;     // load tiles with TMA (16 B aligned base and pitch)
 constexpr int kFrameTmaOut = 2;    // store tiles with TMA
@@ -96,15 +104,19 @@ constexpr int kMaxStages = 3;
 
 // Default strategy and output tile per (pixel size, k), used by handles until
 // tuned and by the allocation-free entry point. Measured on GB300 (tile
-// sweeps of all strategies): the 640x512 14-bit sweep for k <= 7; for the
-// bit-plane windows, 1280x1024 frames with sparse random-valued impulses and
-// the mixed batch's dense k = 15 frames, where a taller strip (16 rows per
-// warp) builds fewer halo rows of planes per output row.
+// sweeps of all strategies): the 640x512 14-bit sweep for k <= 7 (k = 5:
+// dense 128x64 0.097 ms per 128 frames against 0.144 for the network
+// strategy; k = 7: dense 128x128 0.197 against 0.234); for the bit-plane
+// windows, 1280x1024 frames with sparse random-valued impulses and the mixed
+// batch's dense k = 15 frames, where a taller strip (16 rows per warp) builds
+// fewer halo rows of planes per output row.
 struct DefaultTile {
   int algo, tile_w, tile_h;
 };
 __host__ __device__ constexpr DefaultTile default_tile(int /*esize: the same for both pixel sizes*/, int k) {
   return k == 3   ? DefaultTile{ALGO_DENSE3, 128, 64}
+         : k == 5 ? DefaultTile{ALGO_DENSE, 128, 64}
+         : k == 7 ? DefaultTile{ALGO_DENSE, 128, 128}
          : k <= 9 ? DefaultTile{ALGO_NETWORK, 64, 64}
                   : DefaultTile{ALGO_BITPLANE, 32, 128};
 }

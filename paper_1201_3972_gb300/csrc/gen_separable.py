@@ -6,8 +6,8 @@ keeps it only where the detector flags the pixel, so that the work of
 overlapping windows can be shared. Any exact selection gives the same g_m;
 this one is a fixed min/max network, so it is branch-free and integer-exact.
 
-One lane item is a pair of output rows (y, y+1) times eight output columns
-x0..x0+7. The network reads the item's k+1 stage rows as 32-bit words of two
+One lane item is a pair of output rows (y, y+1) times NOUT[k] output columns
+x0 .. x0+NOUT[k]-1. The network reads the item's k+1 stage rows as 32-bit words of two
 16-bit pixels (columns c, c+1: "x-packed") and works in three stages:
 
 1. Vertical (per x-packed word column): the k-1 rows that the windows of
@@ -53,7 +53,7 @@ from typing import Dict, List, Sequence, Tuple
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(HERE, "fnr_separable.cuh")
 KS = (5, 7)
-NOUT = 8          # output columns per lane item
+NOUT = {5: 8, 7: 8}   # output columns per lane item
 NEG, POS = "-inf", "+inf"
 
 # optimal-size sorting networks for small n (D. Knuth, TAOCP 5.3.4)
@@ -225,7 +225,7 @@ def first_word_col(k: int) -> int:
 
 def words_per_row(k: int) -> int:
     R = (k - 1) // 2
-    return (NOUT - 1 + R - first_word_col(k)) // 2 + 1
+    return (NOUT[k] - 1 + R - first_word_col(k)) // 2 + 1
 
 
 def horizontal(p: Prog, col, k: int):
@@ -242,7 +242,7 @@ def horizontal(p: Prog, col, k: int):
 
     outs = []
     if k == 5:
-        for x in range(0, NOUT, 2):
+        for x in range(0, NOUT[k], 2):
             A, B = m2(x - 1), m2(x + 1)             # columns x-1 .. x+2, shared by x and x+1
             S = merge(p, A, B, range(m - k, m + 1))
             smin, smax = p.mn(A[0], B[0]), p.mx(A[-1], B[-1])
@@ -257,7 +257,7 @@ def horizontal(p: Prog, col, k: int):
                 B4[j] = (merge(p, A, B, range(3, 25)), p.mn(A[0], B[0]), p.mx(A[-1], B[-1]))
             return B4[j]
 
-        for x in range(0, NOUT, 2):                  # columns x-2 .. x+3, shared by x and x+1
+        for x in range(0, NOUT[k], 2):               # columns x-2 .. x+3, shared by x and x+1
             if x % 4 == 0:
                 (Bd, bmin, bmax), A = b4(x), m2(x - 2)
             else:
@@ -276,14 +276,25 @@ def item_program(k: int):
     """The whole lane item: inputs r[row][word] (x-packed), outputs per column."""
     p = Prog()
     w0 = first_word_col(k)
+    nw = words_per_row(k)
     cols: Dict[int, List[int]] = {}
+    loaded: Dict[int, List[int]] = {}
+
+    def rows_of(w):
+        if w not in loaded:
+            loaded[w] = [p.inp((r, w)) for r in range(k + 1)]
+        return loaded[w]
 
     def col(c):
         if c not in cols:
-            # the word column's rows are read where first needed, so that few
-            # inputs are live at a time
+            # a word column's rows are read one word column ahead of their
+            # use: few inputs are live at a time, and the loads' latency
+            # overlaps the previous column's work
             w = (c - w0) // 2
-            top, bot = vertical(p, [p.inp((r, w)) for r in range(k + 1)], k)
+            rows = rows_of(w)
+            if w + 1 < nw:
+                rows_of(w + 1)
+            top, bot = vertical(p, rows, k)
             cols[w0 + 2 * w] = [p.lo(top[i], bot[i]) for i in range(k)]
             cols[w0 + 2 * w + 1] = [p.hi(top[i], bot[i]) for i in range(k)]
         return cols[c]
@@ -358,8 +369,9 @@ def emit_item(k: int) -> List[str]:
         done_at.setdefault(max(o[1:]), []).append(o)
     nw = words_per_row(k)
     lines = [f"// k={k}: {c.get('min', 0)} min, {c.get('max', 0)} max, {c.get('lo', 0) + c.get('hi', 0)} permutes"
-             f" per item of {2 * NOUT} pixels",
+             f" per item of {2 * NOUT[k]} pixels",
              f"template <> struct SepNet<{k}> {{",
+             f"  static constexpr int kOut = {NOUT[k]};",
              f"  static constexpr int kRows = {k + 1};",
              f"  static constexpr int kWords = {nw};",
              f"  static constexpr int kFirstCol = {first_word_col(k)};",
@@ -438,7 +450,7 @@ def main() -> None:
         p, outs = item_program(k)
         c = op_counts(live_ops(p, outs))
         mm = c.get("min", 0) + c.get("max", 0)
-        print(f"k={k}: {mm} min/max ({mm / (2 * NOUT):.1f} per pixel), "
+        print(f"k={k}: {mm} min/max ({mm / (2 * NOUT[k]):.1f} per pixel), "
               f"{c.get('lo', 0) + c.get('hi', 0)} permutes per item")
 
 

@@ -176,8 +176,11 @@ static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_conf
     return no("unknown algo");
   if (c.ctas_per_sm < 0) return no("ctas_per_sm < 0");
   if (c.tile_h % tile_h_multiple(k, c.algo)) return no("tile_h must split into 8 warp strips of whole row groups");
-  if ((c.algo == IR_ALGO_DENSE3 || c.algo == IR_ALGO_DENSE) && ((c.tile_w / 8) & (c.tile_w / 8 - 1)))
-    return no("the dense strategies need tile_w / 8 a power of two");
+  if (c.algo == IR_ALGO_DENSE3 || c.algo == IR_ALGO_DENSE) {
+    const int cols = dense_item_cols(c.algo, k);
+    if (c.tile_w % cols || ((c.tile_w / cols) & (c.tile_w / cols - 1)))
+      return no("the dense strategies need tile_w a power-of-two multiple of their item width");
+  }
   const Layout L = make_layout(esize, k, c.algo, c.tile_h, c.tile_w);
   if (L.bw > 256 || L.bh > 256) return no("tile plus halo exceeds the 256-pixel TMA box");
   if (c.tile_w > 256 || c.tile_h > 256) return no("tile side > 256");
@@ -986,6 +989,140 @@ static void tuning_frame(std::vector<unsigned char> &buf, int H, int W, int esiz
     }
 }
 
+// Median time (ms) of `reps` launches of a batch plan of descs[0..n) under
+// configuration c for its (single) class, each launch preceded by a memset of
+// `flush` (flush_bytes, nullable) outside the timed events.
+static ir_status time_config(ir_filter *h, const ir_frame_desc *descs, int n, int es, int k, const ir_kernel_config &c,
+                             int reps, cudaStream_t st, void *flush, size_t flush_bytes, cudaEvent_t e0,
+                             cudaEvent_t e1, float *ms_out) {
+  const ir_kernel_config saved = h->cfg[es - 1][kslot(k)];
+  h->cfg[es - 1][kslot(k)] = c;
+  ir_batch_plan *plan = nullptr;
+  ir_status s = ir_batch_plan_create(h, descs, n, &plan);
+  h->cfg[es - 1][kslot(k)] = saved;
+  if (s != IR_OK) return s;
+  std::vector<float> t;
+  for (int w = 0; w < 2 && s == IR_OK; ++w) s = ir_batch_plan_launch(plan, st);
+  for (int r = 0; r < reps && s == IR_OK; ++r) {
+    if (flush && cudaMemsetAsync(flush, r & 0xff, flush_bytes, st) != cudaSuccess) {
+      s = fail(h, IR_ECUDA, "L2 flush failed");
+      break;
+    }
+    if (cudaEventRecord(e0, st) != cudaSuccess) s = fail(h, IR_ECUDA, "cudaEventRecord failed");
+    if (s == IR_OK) s = ir_batch_plan_launch(plan, st);
+    if (s == IR_OK && cudaEventRecord(e1, st) != cudaSuccess) s = fail(h, IR_ECUDA, "cudaEventRecord failed");
+    float ms = 0;
+    if (s == IR_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      s = fail(h, IR_ECUDA, "timing a tuning launch failed");
+    t.push_back(ms);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && s == IR_OK) s = fail(h, IR_ECUDA, "tuning launch failed");
+  ir_batch_plan_destroy(plan);
+  if (s != IR_OK) return s;
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  return IR_OK;
+}
+
+// Tunes (es, k) on descs[0..n) (frames of that class only); fills *res.
+static ir_status tune_class(ir_filter *h, const ir_frame_desc *descs, int n, int es, int k, int reps, cudaStream_t st,
+                            ir_tune_result *res) {
+  size_t bytes = 0;
+  for (int i = 0; i < n; ++i) bytes += 2 * static_cast<size_t>(descs[i].H) * descs[i].W * es;
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) l2 = 128 << 20;
+  const size_t flush_bytes = 2 * static_cast<size_t>(l2);
+  void *flush = nullptr;
+  if (bytes < flush_bytes && cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, IR_ENOMEM, "cannot allocate the %zu-byte L2 flush buffer for tuning", flush_bytes);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ir_status s = IR_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    s = fail(h, IR_ECUDA, "cudaEventCreate failed");
+  const ir_kernel_config def = default_config(es, k);
+  std::vector<ir_kernel_config> cands = candidates(es, k);
+  bool has_def = false;
+  for (const ir_kernel_config &c : cands)
+    has_def |= c.algo == def.algo && c.tile_w == def.tile_w && c.tile_h == def.tile_h && c.ctas_per_sm == def.ctas_per_sm;
+  if (!has_def) cands.insert(cands.begin(), def);
+  ir_kernel_config best = def;
+  float best_ms = 1e30f, def_ms = 0.f;
+  int timed = 0;
+  for (const ir_kernel_config &c : cands) {
+    if (s != IR_OK) break;
+    if (!config_ok(h, es, k, c, nullptr) || !get_kernel(es, k, c.algo)) continue;
+    float ms = 0.f;
+    s = time_config(h, descs, n, es, k, c, reps, st, flush, flush_bytes, e0, e1, &ms);
+    if (s == IR_EUNSUPPORTED) {  // a shape that does not fit an SM: skip it
+      s = IR_OK;
+      continue;
+    }
+    if (s != IR_OK) break;
+    ++timed;
+    const bool is_def = c.algo == def.algo && c.tile_w == def.tile_w && c.tile_h == def.tile_h &&
+                        c.ctas_per_sm == def.ctas_per_sm;
+    if (is_def) def_ms = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (flush) cudaFree(flush);
+  if (s != IR_OK) return s;
+  if (timed == 0) return fail(h, IR_EUNSUPPORTED, "no configuration could be timed for esize=%d k=%d", es, k);
+  h->cfg[es - 1][kslot(k)] = best;
+  if (res) {
+    res->dtype = es == 1 ? IR_U8 : IR_U16;
+    res->k = k;
+    res->frames = n;
+    res->candidates = timed;
+    res->chosen = best;
+    res->chosen_ms = best_ms;
+    res->defaults = def;
+    res->default_ms = def_ms;
+  }
+  return IR_OK;
+}
+
+ir_status ir_filter_autotune_batch(ir_filter *h, const ir_frame_desc *descs, int n, int reps, void *cuda_stream,
+                                   ir_tune_result *results, int max_results, int *n_results) {
+  fnr::NvtxRange nvtx_range("ir_filter_autotune_batch");
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
+  if (reps < 0 || reps > 100000) return fail(h, IR_EINVAL, "reps must be in [0, 100000]");
+  if (max_results < 0 || (max_results > 0 && !results)) return fail(h, IR_EINVAL, "bad results buffer");
+  if (n_results) *n_results = 0;
+  reps = std::max(reps, 20);
+  for (int i = 0; i < n; ++i) {
+    const ir_frame_desc &d = descs[i];
+    ir_status s = check_frame(h, d.in, d.in_pitch, d.out, d.out_pitch, d.H, d.W, d.dtype, d.k);
+    if (s != IR_OK) return fail(h, s, "frame %d: %s", i, h->last_error.c_str());
+  }
+  DeviceGuard g(h->device);
+  std::map<std::pair<int, int>, std::vector<ir_frame_desc>> groups;
+  for (int i = 0; i < n; ++i) {
+    ir_frame_desc d = descs[i];
+    d.flagged_count = nullptr;  // tuning leaves the caller's counters alone
+    groups[{esize_of(d.dtype), d.k}].push_back(d);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int c = 0;
+  for (auto &kv : groups) {
+    ir_tune_result r{};
+    ir_status s = tune_class(h, kv.second.data(), static_cast<int>(kv.second.size()), kv.first.first, kv.first.second,
+                             reps, st, &r);
+    if (s != IR_OK) return s;
+    if (c < max_results) results[c] = r;
+    ++c;
+  }
+  if (n_results) *n_results = c;
+  return IR_OK;
+}
+
 ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, void *cuda_stream) {
   fnr::NvtxRange nvtx_range("ir_filter_autotune");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
@@ -997,48 +1134,29 @@ ir_status ir_filter_autotune(ir_filter *h, ir_dtype dtype, int k, int H, int W, 
   std::vector<unsigned char> hbuf;
   tuning_frame(hbuf, H, W, es, pitch);
   void *din = nullptr, *dout = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  ir_status result = IR_OK;
-  ir_kernel_config best = h->cfg[es - 1][kslot(k)];
-  const ir_kernel_config saved = best;
-  float best_ms = 1e30f;
-  do {
-    if (cudaMalloc(&din, pitch * H) != cudaSuccess || cudaMalloc(&dout, pitch * H) != cudaSuccess) {
-      cudaGetLastError();
-      result = fail(h, IR_ENOMEM, "cannot allocate tuning frames");
-      break;
-    }
-    if (cudaMemcpy(din, hbuf.data(), pitch * H, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-      result = fail(h, IR_ECUDA, "tuning setup failed");
-      break;
-    }
-    for (const ir_kernel_config &c : candidates(es, k)) {
-      if (!config_ok(h, es, k, c, nullptr) || !get_kernel(es, k, c.algo)) continue;
-      h->cfg[es - 1][kslot(k)] = c;
-      bool bad = false;
-      for (int w = 0; w < 2 && !bad; ++w)
-        bad = run_one(h, din, pitch, dout, pitch, H, W, dtype, k, st, nullptr) != IR_OK;
-      if (bad) continue;
-      const int reps = 5;
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && !bad; ++r) bad = run_one(h, din, pitch, dout, pitch, H, W, dtype, k, st, nullptr) != IR_OK;
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess || bad) continue;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
-    }
-  } while (false);
-  h->cfg[es - 1][kslot(k)] = (result == IR_OK && best_ms < 1e30f) ? best : saved;
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (din) cudaFree(din);
-  if (dout) cudaFree(dout);
-  return result;
+  if (cudaMalloc(&din, pitch * H) != cudaSuccess || cudaMalloc(&dout, pitch * H) != cudaSuccess) {
+    cudaGetLastError();
+    if (din) cudaFree(din);
+    return fail(h, IR_ENOMEM, "cannot allocate tuning frames");
+  }
+  ir_status s = IR_OK;
+  if (cudaMemcpy(din, hbuf.data(), pitch * H, cudaMemcpyHostToDevice) != cudaSuccess)
+    s = fail(h, IR_ECUDA, "tuning setup failed");
+  if (s == IR_OK) {
+    ir_frame_desc d{};
+    d.in = din;
+    d.out = dout;
+    d.H = H;
+    d.W = W;
+    d.in_pitch = d.out_pitch = pitch;
+    d.dtype = dtype;
+    d.k = k;
+    d.flagged_count = nullptr;
+    s = tune_class(h, &d, 1, es, k, 20, st, nullptr);
+  }
+  cudaFree(din);
+  cudaFree(dout);
+  return s;
 }
 
 }  // extern "C"

@@ -327,9 +327,59 @@ def test_autotune_keeps_results_exact(flt):
     for k in (3, 5, 9):
         flt.autotune(_lib.IR_U14, k, 512, 640)
         cfg = flt.get_config(_lib.IR_U14, k)
-        assert cfg["algo"] in (_lib.IR_ALGO_DENSE3, _lib.IR_ALGO_NETWORK, _lib.IR_ALGO_BITPLANE)
+        assert cfg["algo"] in algos_for(k)
         check(flt, f, k, u14=True)
         flt.set_config(_lib.IR_U14, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+def test_autotune_batch_on_the_callers_frames(flt):
+    """ir_filter_autotune_batch tunes each class on the given frames: every
+    class is reported with its candidates timed, the choice is no slower than
+    the default in the tuner's own timing (the default is one of the
+    candidates), the tuned plan's results equal the oracle's, and a fresh
+    timing of the tuned plan is not slower than the default plan's."""
+    import statistics
+    import torch
+    specs = synth.workload_sweep_u14()
+    frames = [s.make() for s in specs]
+    reps = 4
+    ins = [torch.from_numpy(f.view(np.int16)).cuda() for f in frames * reps]
+    outs = [torch.empty_like(t) for t in ins]
+    descs = flt.make_descs([{"in": a, "out": b, "k": specs[i % len(specs)].k, "u14": True}
+                            for i, (a, b) in enumerate(zip(ins, outs))])
+    try:
+        res = flt.autotune_batch(descs, reps=20)
+        assert sorted(r["k"] for r in res) == [3, 5, 7]
+        for r in res:
+            assert r["dtype"] == _lib.IR_U16 and r["frames"] == reps * 4 and r["candidates"] >= 2
+            assert 0 < r["chosen_ms"] <= r["default_ms"] * (1 + 1e-6)
+            assert flt.get_config(_lib.IR_U14, r["k"]) == r["chosen"]
+        plan = _lib.BatchPlan(flt, descs)
+        plan.launch()
+        torch.cuda.synchronize()
+        for i, o in enumerate(outs[:len(specs)]):
+            want, _ = oracle.fnr(frames[i], specs[i].k)
+            np.testing.assert_array_equal(o.cpu().numpy().view(np.uint16), want)
+
+        def timed(p):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(30)]
+            for a, b in ev:
+                a.record()
+                p.launch()
+                b.record()
+            torch.cuda.synchronize()
+            return statistics.median(a.elapsed_time(b) for a, b in ev)
+        t_tuned = timed(plan)
+        plan.close()
+        for r in res:
+            flt.set_config(_lib.IR_U14, r["k"], 0, 0, _lib.IR_ALGO_AUTO)
+        dplan = _lib.BatchPlan(flt, descs)
+        t_default = timed(dplan)
+        dplan.close()
+        assert t_tuned <= 1.10 * t_default, (t_tuned, t_default)
+    finally:
+        for k in (3, 5, 7):
+            flt.set_config(_lib.IR_U14, k, 0, 0, _lib.IR_ALGO_AUTO)
 
 
 def test_launch_counter_counts_kernels(flt):
