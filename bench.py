@@ -465,13 +465,13 @@ def own_arm(args):
         dist.destroy_process_group()
 
 
-def tune_summary(r: dict) -> dict:
+def tune_summary(r: dict) -> str:
+    """'<algo> <tile>, x<speedup> vs default <algo> <tile>, <n> candidates'."""
     from paper_1201_3972_gb300 import _lib
     c, d = r["chosen"], r["defaults"]
-    return {"algo": _lib.ALGO_NAMES[c["algo"]], "tile": f"{c['tile_w']}x{c['tile_h']}",
-            "default": f"{_lib.ALGO_NAMES[d['algo']]} {d['tile_w']}x{d['tile_h']}",
-            "speedup_vs_default": round(r["default_ms"] / r["chosen_ms"], 3) if r["chosen_ms"] > 0 else None,
-            "candidates": r["candidates"]}
+    sp = r["default_ms"] / r["chosen_ms"] if r["chosen_ms"] > 0 else float("nan")
+    return (f"{_lib.ALGO_NAMES[c['algo']]} {c['tile_w']}x{c['tile_h']}, x{sp:.3f} vs default "
+            f"{_lib.ALGO_NAMES[d['algo']]} {d['tile_w']}x{d['tile_h']}, {r['candidates']} candidates")
 
 
 def summary(r: dict) -> dict:
@@ -511,6 +511,19 @@ def batch_leg(flt, stream, args):
                             for i, s in enumerate(specs)])
     tuned = flt.autotune_batch(every, reps=20, stream=stream)
     out["tuned"] = {f"{'u8' if r['dtype'] == _lib.IR_U8 else 'u16'} k{r['k']}": tune_summary(r) for r in tuned}
+    # each (pixel type, k) class alone: where the mixed batch's time goes
+    alone = {}
+    for key in sorted({(s.dtype == synth.U8, s.k) for s in specs}):
+        idx = [i for i, s in enumerate(specs) if (s.dtype == synth.U8, s.k) == key]
+        plan = flt.plan([{"in": bufs[i][0], "out": bufs[i][1], "k": specs[i].k, "u14": specs[i].dtype == synth.U14}
+                         for i in idx])
+        for _ in range(args.warmup):
+            plan.launch(stream)
+        alone[f"{'u8' if key[0] else 'u16'} k{key[1]}"] = round(statistics.median(
+            time_events(torch, lambda: plan.launch(stream), LEG_ITERS // 2, stream, flush=True)), 4)
+        plan.close()
+    out["classes_alone_ms"] = alone
+    out["classes_alone_sum_ms"] = round(sum(alone.values()), 4)
     for name, sel in (("all", lambda s: True), ("k3_k5", lambda s: s.k in (3, 5))):
         idx = [i for i, s in enumerate(specs) if sel(s)]
         plan = flt.plan([{"in": bufs[i][0], "out": bufs[i][1], "k": specs[i].k, "u14": specs[i].dtype == synth.U14}

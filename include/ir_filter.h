@@ -91,7 +91,11 @@ typedef enum {
 
 /* Kernel configuration for one (dtype, k) class. tile_w, tile_h: output tile
  * in pixels (multiples of 8; tile_w + halo <= 256 pixels). ctas_per_sm: 0 = as
- * many as fit. */
+ * many as fit. A launch whose frames give fewer tiles than the GPU has SMs
+ * (a small single frame, a small batch class) runs the same strategy with
+ * its tile halved, height first, while the tiles do not cover the SMs and the
+ * tile keeps at least 4096 pixels (unless ir_filter_set_tile_fit turns this
+ * off). */
 typedef struct {
   int tile_w;
   int tile_h;
@@ -245,6 +249,12 @@ ir_border ir_filter_get_border(const ir_filter *h);
  * Frames whose row (W * bytes per pixel) is not a multiple of 16 bytes are
  * accepted either way (their right-edge tiles use plain stores). */
 ir_status ir_filter_set_strict_alignment(ir_filter *h, int on);
+
+/* Tile fitting for the handle's later calls and plans (on != 0, the
+ * default): a launch whose frames give fewer tiles than the GPU has SMs
+ * shrinks its tile as described at ir_kernel_config. Off, every launch uses
+ * the table's tile as it is (e.g. to time or test one exact shape). */
+ir_status ir_filter_set_tile_fit(ir_filter *h, int on);
 
 /* Noise detector for the handle's later calls, like ir_filter_set_border
  * (single frames, in place, passes, batch plans created afterwards; tuning

@@ -32,7 +32,7 @@ EXPORTED = (
     "ir_filter_sync_status", "ir_filter_autotune", "ir_filter_get_config", "ir_filter_set_config",
     "ir_filter_launch_count", "ir_status_string", "ir_filter_last_error", "ir_filter_version",
     "ir_filter_run_noalloc", "ir_filter_noalloc_status", "ir_filter_median_filter", "ir_filter_run_passes", "ir_filter_set_border",
-    "ir_filter_get_border", "ir_filter_set_detector", "ir_filter_get_detector", "ir_filter_set_strict_alignment",
+    "ir_filter_get_border", "ir_filter_set_tile_fit", "ir_filter_set_detector", "ir_filter_get_detector", "ir_filter_set_strict_alignment",
     "ir_filter_run_host", "ir_filter_autotune_batch",
     "ir_server_create", "ir_server_destroy", "ir_server_filter", "ir_server_open_stream", "ir_server_close_stream",
     "ir_server_submit", "ir_server_poll", "ir_server_wait_idle", "ir_server_output", "ir_server_read",
@@ -136,6 +136,7 @@ def load(path: Optional[str] = None):
             "ir_filter_set_detector": ([vp, i32], i32),
             "ir_filter_get_detector": ([vp], i32),
             "ir_filter_set_strict_alignment": ([vp, i32], i32),
+            "ir_filter_set_tile_fit": ([vp, i32], i32),
             "ir_filter_run_passes": ([vp, vp, sz, vp, sz, i32, i32, i32, i32, i32, vp, vp], i32),
             "ir_server_create": ([i32, ctypes.POINTER(ir_server_config), ctypes.POINTER(vp)], i32),
             "ir_server_destroy": ([vp], None),
@@ -270,6 +271,10 @@ class Filter:
 
     def get_detector(self) -> int:
         return int(self.lib.ir_filter_get_detector(self.h))
+
+    def set_tile_fit(self, on: bool) -> None:
+        """Shrink the tile of launches that cannot fill the GPU (default on)."""
+        _check(self.lib, self.h, self.lib.ir_filter_set_tile_fit(self.h, 1 if on else 0))
 
     def set_strict_alignment(self, on: bool) -> None:
         """Refuse (IR_EALIGN) frames whose base or pitch is not 16-byte aligned

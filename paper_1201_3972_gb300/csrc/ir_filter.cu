@@ -77,6 +77,7 @@ struct ir_filter {
   int border = kBorderReplicate;
   int detector = kModeFnr;  // kModeFnr (Eq. 3a/3b) or kModeDirectional
   bool strict_align = false;  // misaligned frames are refused (IR_EALIGN) instead of staged with plain loads
+  bool tile_fit = true;       // launches with fewer tiles than SMs shrink their tile (fit_tile)
   std::string last_error;
   std::map<std::pair<const void *, int>, int> occupancy;  // (kernel, smem) -> CTAs per SM
   std::map<const void *, int> smem_attr;                  // kernel -> dynamic smem attribute set
@@ -186,6 +187,29 @@ static bool config_ok(const ir_filter *h, int esize, int k, const ir_kernel_conf
   if (c.tile_w > 256 || c.tile_h > 256) return no("tile side > 256");
   if (h && L.total > h->max_smem) return no("tile needs more shared memory than a CTA can have");
   return true;
+}
+
+// A class whose frames give fewer tiles than the GPU has SMs would leave SMs
+// idle: its tile shrinks (height first, then width, keeping the strategy and
+// at least 4096 pixels per tile, so that every consumer warp still has a lane
+// item per lane) until the tiles cover the SMs or it cannot shrink further.
+static ir_kernel_config fit_tile(const ir_filter *h, int es, int k, ir_kernel_config c, const int *Hs, const int *Ws,
+                                 int n) {
+  auto tiles = [&](const ir_kernel_config &x) {
+    long long t = 0;
+    for (int i = 0; i < n; ++i)
+      t += static_cast<long long>((Ws[i] + x.tile_w - 1) / x.tile_w) * ((Hs[i] + x.tile_h - 1) / x.tile_h);
+    return t;
+  };
+  while (h->tile_fit && tiles(c) < h->sm_count) {
+    ir_kernel_config a = c, b = c;
+    a.tile_h /= 2;
+    b.tile_w /= 2;
+    if (a.tile_h * a.tile_w >= 4096 && config_ok(h, es, k, a, nullptr)) c = a;
+    else if (b.tile_h * b.tile_w >= 4096 && config_ok(h, es, k, b, nullptr)) c = b;
+    else break;
+  }
+  return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +350,7 @@ static ir_status run_one(ir_filter *h, const void *in, size_t in_pitch, void *ou
   ClassLaunch cl;
   cl.esize = esize_of(dtype);
   cl.k = k;
-  cl.cfg = h->cfg[cl.esize - 1][kslot(k)];
+  cl.cfg = fit_tile(h, cl.esize, k, h->cfg[cl.esize - 1][kslot(k)], &H, &W, 1);
   cl.prm = FnrParams{};
   host_make_frame_dev(h, cl.prm.single, in, in_pitch, out, out_pitch, H, W, cl.esize, k, cl.cfg, flagged);
   cl.prm.table = nullptr;
@@ -541,6 +565,12 @@ ir_status ir_filter_set_strict_alignment(ir_filter *h, int on) {
   return IR_OK;
 }
 
+ir_status ir_filter_set_tile_fit(ir_filter *h, int on) {
+  if (!h) return fail(nullptr, IR_EINVAL, "null handle");
+  h->tile_fit = on != 0;
+  return IR_OK;
+}
+
 ir_status ir_filter_set_detector(ir_filter *h, ir_detector detector) {
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (detector != IR_DETECT_EXTREME && detector != IR_DETECT_DIRECTIONAL)
@@ -610,7 +640,15 @@ ir_status ir_batch_plan_create(ir_filter *h, const ir_frame_desc *descs, int n, 
     ClassLaunch cl;
     cl.esize = kv.first.first;
     cl.k = kv.first.second;
-    cl.cfg = h->cfg[cl.esize - 1][kslot(cl.k)];
+    {
+      std::vector<int> Hs, Ws;
+      for (int i : kv.second) {
+        Hs.push_back(descs[i].H);
+        Ws.push_back(descs[i].W);
+      }
+      cl.cfg = fit_tile(h, cl.esize, cl.k, h->cfg[cl.esize - 1][kslot(cl.k)], Hs.data(), Ws.data(),
+                        static_cast<int>(Hs.size()));
+    }
     int tiles = 0;
     const int first = slot;
     for (int i : kv.second) {
@@ -718,17 +756,26 @@ void ir_batch_plan_destroy(ir_batch_plan *plan) {
   delete plan;
 }
 
+// A plan is reused for the same descriptors under the same handle settings.
+static PlanKey plan_key(const ir_filter *h, const ir_frame_desc *descs, int n) {
+  PlanKey key;
+  auto put = [&](const void *p, size_t len) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    key.bytes.insert(key.bytes.end(), b, b + len);
+  };
+  put(descs, sizeof(ir_frame_desc) * n);
+  put(h->cfg, sizeof(h->cfg));
+  put(&h->border, sizeof(h->border));
+  put(&h->detector, sizeof(h->detector));
+  put(&h->tile_fit, sizeof(h->tile_fit));
+  return key;
+}
+
 ir_status ir_filter_run_batch(ir_filter *h, const ir_frame_desc *descs, int n, void *cuda_stream) {
   fnr::NvtxRange nvtx_range("ir_filter_run_batch");
   if (!h) return fail(nullptr, IR_EINVAL, "null handle");
   if (n < 1 || !descs) return fail(h, IR_EINVAL, "empty batch");
-  PlanKey key;
-  key.bytes.resize(sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
-  std::memcpy(key.bytes.data(), descs, sizeof(ir_frame_desc) * n);
-  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n, h->cfg, sizeof(h->cfg));
-  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n + sizeof(h->cfg), &h->border, sizeof(h->border));
-  std::memcpy(key.bytes.data() + sizeof(ir_frame_desc) * n + sizeof(h->cfg) + sizeof(h->border), &h->detector,
-              sizeof(h->detector));
+  const PlanKey key = plan_key(h, descs, n);
   auto it = h->plans.find(key);
   ir_batch_plan *plan = nullptr;
   if (it != h->plans.end()) {
@@ -914,14 +961,7 @@ static ir_status host_chunk(ir_filter *h, const ir_frame_desc *descs, const ir_f
   IR_CUDA(h, cudaEventRecord(ev_in, s_in));
   IR_CUDA(h, cudaStreamWaitEvent(s_filter, ev_in, 0));
   // the chunk's plan, rebuilt when its frames or the handle's settings change
-  PlanKey key;
-  key.bytes.resize(sizeof(ir_frame_desc) * (b - a) + sizeof(h->cfg) + sizeof(h->border) + sizeof(h->detector));
-  unsigned char *kp = key.bytes.data();
-  std::memcpy(kp, dd + a, sizeof(ir_frame_desc) * (b - a));
-  kp += sizeof(ir_frame_desc) * (b - a);
-  std::memcpy(kp, h->cfg, sizeof(h->cfg));
-  std::memcpy(kp + sizeof(h->cfg), &h->border, sizeof(h->border));
-  std::memcpy(kp + sizeof(h->cfg) + sizeof(h->border), &h->detector, sizeof(h->detector));
+  const PlanKey key = plan_key(h, dd + a, b - a);
   if (!h->host_plans[c] || !(h->host_keys[c] == key)) {
     if (h->host_plans[c]) {
       // the old plan may still run on one of the copy streams

@@ -41,6 +41,7 @@ def tiles_for(es, k, algo):
 def main() -> int:
     assert os.path.basename(_lib.library_path()) == "libirfnr_debug.so", _lib.library_path()
     flt = _lib.Filter(0)
+    flt.set_tile_fit(False)   # every tile shape exactly as configured
     rng = np.random.default_rng(2026)
     runs = 0
     for k in (3, 5, 7, 9, 11, 15, 21):

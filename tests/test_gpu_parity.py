@@ -5,6 +5,8 @@ buffers and compares every output pixel, and the flagged count, with the
 oracle on the same seeded input. Sizes span several tiles plus ragged tails;
 the workload tests run the full frame sizes the benchmark times.
 """
+import contextlib
+
 import numpy as np
 import pytest
 
@@ -96,6 +98,17 @@ def with_config(flt, dtype, k, algo, tw, th):
     flt.set_config(dtype, k, tw, th, algo)
 
 
+@contextlib.contextmanager
+def exact_tiles(flt):
+    """Launches use the configured tile as it is (no shrinking of launches
+    with fewer tiles than SMs), so that a sweep tests exactly its shapes."""
+    flt.set_tile_fit(False)
+    try:
+        yield
+    finally:
+        flt.set_tile_fit(True)
+
+
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("fx", all_fixtures(), ids=lambda f: f["name"])
 def test_golden_fixtures_every_algo(flt, fx):
@@ -125,6 +138,12 @@ def test_every_algo_and_tile_random(flt, k, es):
     npdt = np.uint8 if es == 1 else np.uint16
     maxv = 255 if es == 1 else 65535
     shapes = [(67, 150), (33, 29)]
+    with exact_tiles(flt):
+        _sweep_random(flt, k, es, dt, npdt, maxv, rng, shapes)
+    flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
+
+
+def _sweep_random(flt, k, es, dt, npdt, maxv, rng, shapes):
     for algo in algos_for(k):
         for tw, th in tiles_for(es, k, algo):
             try:
@@ -137,7 +156,6 @@ def test_every_algo_and_tile_random(flt, k, es):
                 check(flt, a, k)
                 b = rng.choice([0, 1, maxv // 2, maxv], (H, W)).astype(npdt)
                 check(flt, b, k)
-    flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
 
 
 @pytest.mark.parametrize("k", ALL_K)
@@ -151,16 +169,17 @@ def test_every_algo_and_tile_on_the_tma_path(flt, k, es):
     dt = _lib.IR_U8 if es == 1 else _lib.IR_U16
     npdt = np.uint8 if es == 1 else np.uint16
     maxv = 255 if es == 1 else 65535
-    for algo in algos_for(k):
-        for tw, th in tiles_for(es, k, algo):
-            try:
-                flt.set_config(dt, k, tw, th, algo)
-            except _lib.IrError as e:
-                assert e.status == _lib.IR_EINVAL
-                continue
-            for H, W in ((67, 150), (33, 29)):
-                pitch = -(-W * es // 16) * 16 // es
-                check(flt, rng.integers(0, maxv + 1, (H, W)).astype(npdt), k, in_pitch=pitch, out_pitch=pitch)
+    with exact_tiles(flt):
+        for algo in algos_for(k):
+            for tw, th in tiles_for(es, k, algo):
+                try:
+                    flt.set_config(dt, k, tw, th, algo)
+                except _lib.IrError as e:
+                    assert e.status == _lib.IR_EINVAL
+                    continue
+                for H, W in ((67, 150), (33, 29)):
+                    pitch = -(-W * es // 16) * 16 // es
+                    check(flt, rng.integers(0, maxv + 1, (H, W)).astype(npdt), k, in_pitch=pitch, out_pitch=pitch)
     flt.set_config(dt, k, 0, 0, _lib.IR_ALGO_AUTO)
     flt.sync_status()
 
@@ -243,12 +262,17 @@ def test_workload_small_k_full_size(flt, spec):
     full frames, every algo."""
     f = spec.make()
     want, wf = oracle.fnr(f, spec.k)
-    for algo in algos_for(spec.k):
-        flt.set_config(spec.dtype, spec.k, 128 if algo in DENSE_ALGOS else 64, 64, algo)
-        got, gf = gpu_fnr(flt, f, spec.k, u14=spec.dtype == _lib.IR_U14)
-        np.testing.assert_array_equal(got, want)
-        assert gf == wf
+    with exact_tiles(flt):
+        for algo in algos_for(spec.k):
+            flt.set_config(spec.dtype, spec.k, 128 if algo in DENSE_ALGOS else 64, 64, algo)
+            got, gf = gpu_fnr(flt, f, spec.k, u14=spec.dtype == _lib.IR_U14)
+            np.testing.assert_array_equal(got, want)
+            assert gf == wf
     flt.set_config(spec.dtype, spec.k, 0, 0, _lib.IR_ALGO_AUTO)
+    # the default configuration with tile fitting (a single frame shrinks its tile)
+    got, gf = gpu_fnr(flt, f, spec.k, u14=spec.dtype == _lib.IR_U14)
+    np.testing.assert_array_equal(got, want)
+    assert gf == wf
 
 
 @pytest.mark.parametrize("spec", synth.workload_large_k(), ids=lambda s: s.tag)
