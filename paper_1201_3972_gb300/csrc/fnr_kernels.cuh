@@ -346,20 +346,19 @@ struct PackedOp {
   }
 };
 
-#ifndef FNR_DENSE_CX_PERIOD
-#define FNR_DENSE_CX_PERIOD 8
-#endif
-#ifndef FNR_DENSE_CX_ALU
-#define FNR_DENSE_CX_ALU 1
-#endif
-
 // The separable networks of the dense 5x5 / 7x7 strategy issue little but
-// min/max, so the ALU pipe alone bounds them: all but one in
-// FNR_DENSE_CX_PERIOD of their exchanges take the max on the FMA pipe.
+// min/max, so the ALU pipe bounds them: of every kPeriod exchanges, kAlu take
+// the ALU max and the others the FMA-pipe form. Measured on GB300 (640x512
+// sweep, 128 frames per class): k = 5 with 1 of 8 on the ALU 0.0968 ms
+// against 0.1029 with 2 of 5 (eight consumer warps per SM at two CTAs); k = 7,
+// whose registers allow one CTA per SM, 0.1933 ms with 2 of 5 against 0.1971
+// with 1 of 8 (fewer warps to hide the longer multiply-add chain).
+template <int K>
 struct DenseOp : PackedOp {
+  static constexpr int kPeriod = K == 5 ? 8 : 5, kAlu = K == 5 ? 1 : 2;
   template <int J>
   __device__ __forceinline__ uint32_t cmax(uint32_t a, uint32_t b, uint32_t lo) const {
-    if (J % FNR_DENSE_CX_PERIOD < FNR_DENSE_CX_ALU) return vmax2(a, b);
+    if (J % kPeriod < kAlu) return vmax2(a, b);
     return imad(lo, neg, imad(a, unit, b));
   }
 };
@@ -601,7 +600,7 @@ __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, i
       }
     }
     uint32_t res[NO];
-    Net::run(DenseOp{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
+    Net::run(DenseOp<K>{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
              DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
