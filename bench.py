@@ -257,7 +257,9 @@ def own_arm(args):
 
     all_idx = list(range(nframes))
     # the autotuner picks each class's strategy and tile on these frames
-    tuned = {str(r["k"]): r for r in flt.autotune_batch(descs_for(all_idx), reps=20, stream=stream)}
+    # (--no-tune, for profiling runs: the library's default table)
+    tuned = {} if args.no_tune else \
+        {str(r["k"]): r for r in flt.autotune_batch(descs_for(all_idx), reps=20, stream=stream)}
     plan = _lib.BatchPlan(flt, descs_for(all_idx))
     launches_per_step = plan.kernel_count
     step_px = nframes * fpx
@@ -509,7 +511,7 @@ def batch_leg(flt, stream, args):
     out = {}
     every = flt.make_descs([{"in": bufs[i][0], "out": bufs[i][1], "k": s.k, "u14": s.dtype == synth.U14}
                             for i, s in enumerate(specs)])
-    tuned = flt.autotune_batch(every, reps=20, stream=stream)
+    tuned = [] if args.no_tune else flt.autotune_batch(every, reps=20, stream=stream)
     out["tuned"] = {f"{'u8' if r['dtype'] == _lib.IR_U8 else 'u16'} k{r['k']}": tune_summary(r) for r in tuned}
     # each (pixel type, k) class alone: where the mixed batch's time goes
     alone = {}
@@ -597,7 +599,7 @@ def large_k_leg(flt, stream, args):
             arr[j].dtype = _lib.IR_U14
             arr[j].k = s.k
             arr[j].flagged_count = None
-        tr = flt.autotune_batch(arr, reps=20, stream=stream)[0]
+        tr = None if args.no_tune else flt.autotune_batch(arr, reps=20, stream=stream)[0]
         plan = _lib.BatchPlan(flt, arr)
         for _ in range(args.warmup):
             plan.launch(stream)
@@ -605,7 +607,8 @@ def large_k_leg(flt, stream, args):
                                            flush=True))
         px = copies * H * W
         out[str(s.k)] = {"frames": copies, "ms": round(ms, 4), "mpx_s": round(px / ms / 1e3, 1),
-                         "hbm_frac": round(px * 4 / (ms * 1e-3) / 1e9 / hbm, 4), "tuned": tune_summary(tr)}
+                         "hbm_frac": round(px * 4 / (ms * 1e-3) / 1e9 / hbm, 4),
+                         "tuned": tune_summary(tr) if tr else "default table (--no-tune)"}
         plan.close()
     return out
 
@@ -732,6 +735,8 @@ def main():
     ap.add_argument("--no-quality", action="store_true", help="skip the Table 1 style PSNR comparison")
     ap.add_argument("--no-directional", action="store_true", help="skip the directional-detector leg")
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pipeline chunks of the end-to-end host-frame call")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner and run the library's default table (profiling runs)")
     ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:
