@@ -289,6 +289,23 @@ def own_arm(args):
         gpu_launches = int(lt.item())
     if world > 1:
         dist.barrier()
+    if args.profile_only:
+        # profiling runs (under ncu): the step and, if asked, the large-window
+        # leg; the line carries only what was run
+        ms_step = total_ms / args.steps
+        out = {"metric": METRIC, "value": round(world * step_px / (ms_step * 1e-3) / 1e6, 1), "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+               "profile_only": args.profile_only, "config": bench_config(R)}
+        if args.profile_only == "large_k" and rank == 0:
+            out["large_k"] = large_k_leg(flt, stream, args)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        plan.close()
+        flt.close()
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     # per-window classes timed alone (the dominant-kernel roofline comes from these)
     per_k = {}
     hbm_peak, peak_kind = peaks()
@@ -737,6 +754,8 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=16, help="pipeline chunks of the end-to-end host-frame call")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner and run the library's default table (profiling runs)")
+    ap.add_argument("--profile-only", choices=["step", "large_k"], default=None,
+                    help="profiling runs: the timed step only, or the step and the large-window leg")
     ap.add_argument("--serve-pool", type=int, default=30, help="pre-generated frames per resolution")
     args = ap.parse_args()
     if args.warmup < 3:
