@@ -527,8 +527,6 @@ struct DenseLoad {
   }
 };
 
-// The detector and the counting are launch-wide (MODE < 0: read from `mode`
-// and `count` at run time, so that one copy of the network serves every mode).
 template <typename T, int K, bool COUNT, int MODE>
 struct DenseEmit {
   using Net = SepNet<K>;
@@ -540,14 +538,8 @@ struct DenseEmit {
   const PackedOp op;
   const int tx, ty, tw_valid, th_valid;
   int &flagged;
-  const int mode;
-  const bool count;
   template <int J>
   __device__ __forceinline__ void put(uint32_t gm, uint32_t gmin, uint32_t gmax) {
-    if constexpr (MODE < 0) {
-      put_runtime<J>(gm, gmin, gmax);
-      return;
-    }
     // the centre pixels of output column x0 + J in rows y and y + 1 (row-packed)
     uint32_t c;
     if constexpr (sizeof(T) == 2) {
@@ -574,36 +566,11 @@ struct DenseEmit {
       flagged += __popc((sig ^ 0x00010001u) & valid);
     }
   }
-  template <int J>
-  __device__ __forceinline__ void put_runtime(uint32_t gm, uint32_t gmin, uint32_t gmax) {
-    uint32_t c;
-    if constexpr (sizeof(T) == 2) {
-      const uint32_t a = *reinterpret_cast<const uint32_t *>(centre + (J & ~1));
-      const uint32_t b = *reinterpret_cast<const uint32_t *>(centre + BW + (J & ~1));
-      c = (J & 1) ? __byte_perm(a, b, 0x7632) : __byte_perm(a, b, 0x5410);
-    } else {
-      c = __byte_perm(static_cast<uint32_t>(centre[J]), static_cast<uint32_t>(centre[BW + J]), 0x5410);
-    }
-    uint32_t sig = vmin2(vmin2(op.sub(c, gmin), op.sub(gmax, c)), 0x00010001u);
-    if (mode == kModeDirectional)
-      sig = (J & 1) ? __byte_perm(dsig[0][J >> 1], dsig[1][J >> 1], 0x7632)
-                    : __byte_perm(dsig[0][J >> 1], dsig[1][J >> 1], 0x5410);
-    else if (mode == kModeMedian)
-      sig = 0u;
-    const uint32_t keep = sig * 0xffffu;
-    res[J] = (c & keep) | (gm & ~keep);
-    if (count) {
-      const uint32_t valid =
-          tx + J < tw_valid ? ((ty < th_valid ? 1u : 0u) | (ty + 1 < th_valid ? 0x10000u : 0u)) : 0u;
-      flagged += __popc((sig ^ 0x00010001u) & valid);
-    }
-  }
 };
 
 template <typename T, int K, bool COUNT, int MODE>
 __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, int BW, int r0, int SR, int seg_shift,
-                                int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged, const PackedOp op,
-                                int mode = MODE, bool count = COUNT) {
+                                int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged, const PackedOp op) {
   using Net = SepNet<K>;
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
@@ -619,7 +586,7 @@ __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, i
     const int tx = sx * NO, ty = r0 + (ry << 1);
     const T *const item = S + ty * BW + XOFF + tx;  // stage row ty, output column x0
     uint32_t dsig[2][NO / 2] = {};
-    if (MODE == kModeDirectional || (MODE < 0 && mode == kModeDirectional)) {
+    if constexpr (MODE == kModeDirectional) {
       // the line test on rows y (stage row ty + R) and y + 1, eight columns at a time
 #pragma unroll
       for (int g = 0; g < NO / 8; ++g) {
@@ -634,8 +601,7 @@ __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, i
     }
     uint32_t res[NO];
     Net::run(DenseOp<K>{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
-             DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged,
-                                          mode, count});
+             DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
 #pragma unroll
     for (int o = 0; o < 2; ++o) {
       if (ty + o < th_valid) {
@@ -1459,21 +1425,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
           dense_sep_strip<T, K, decltype(count)::value, decltype(mode)::value>(
               S, cf, x0, y0, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane, flagged, d3op);
       };
-#ifdef FNR_DENSE_RUNTIME_MODE
-      if constexpr (ALGO == ALGO_DENSE && (K == 5 || K == 7)) {
-        const bool count = p.mode == kModeDirectional || (p.mode == kModeFnr && cur.counted);
-        dense_sep_strip<T, K, false, -1>(S, cf, x0, y0, BW, r0, SR, seg_shift, cur.W - x0, cur.H - y0, vec_ok, lane,
-                                         flagged, d3op, p.mode, count);
-        if (count) {
-          flagged = __reduce_add_sync(0xffffffffu, flagged);
-          if (cur.counted && lane == 0 && flagged != 0) atomicAdd(cf->flagged, static_cast<unsigned long long>(flagged));
-        } else if (p.mode == kModeMedian && cur.counted && lane == 0) {
-          const int rows = min(SR, cur.H - y0 - r0), cols = min(TW, cur.W - x0);
-          atomicAdd(cf->flagged, static_cast<unsigned long long>(rows) * static_cast<unsigned long long>(cols));
-        }
-      } else
-#endif
-
       if (p.mode == kModeMedian) {
         strip(Bool<false>{}, Int<kModeMedian>{});
         if (cur.counted && lane == 0) {  // every in-frame pixel of the strip takes a median
