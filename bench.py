@@ -19,6 +19,7 @@ replica bit for bit).
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import os
 import statistics
@@ -113,8 +114,15 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # never outlive the bench (a profiler waits for every process it started)
+            atexit.register(self._end)
         except Exception:
             self.proc = None
+
+    def _end(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
+            self.proc.wait()
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -125,6 +133,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+            self.proc.wait()
         self.fh.close()
         sms, maxes, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -292,6 +301,7 @@ def own_arm(args):
     if args.profile_only:
         # profiling runs (under ncu): the step and, if asked, the large-window
         # leg; the line carries only what was run
+        clocks.stop()
         ms_step = total_ms / args.steps
         out = {"metric": METRIC, "value": round(world * step_px / (ms_step * 1e-3) / 1e6, 1), "unit": UNIT,
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -485,12 +495,14 @@ def own_arm(args):
 
 
 def tune_summary(r: dict) -> str:
-    """'<algo> <tile>, x<speedup> vs default <algo> <tile>, <n> candidates'."""
+    """'<algo> <tile> x<speedup over the default>/<candidates timed>', plus the
+    default's name when the tuner chose something else."""
     from paper_1201_3972_gb300 import _lib
     c, d = r["chosen"], r["defaults"]
     sp = r["default_ms"] / r["chosen_ms"] if r["chosen_ms"] > 0 else float("nan")
-    return (f"{_lib.ALGO_NAMES[c['algo']]} {c['tile_w']}x{c['tile_h']}, x{sp:.3f} vs default "
-            f"{_lib.ALGO_NAMES[d['algo']]} {d['tile_w']}x{d['tile_h']}, {r['candidates']} candidates")
+    name = lambda x: f"{_lib.ALGO_NAMES[x['algo']]} {x['tile_w']}x{x['tile_h']}"
+    same = (c["algo"], c["tile_w"], c["tile_h"]) == (d["algo"], d["tile_w"], d["tile_h"])
+    return f"{name(c)} x{sp:.3f}/{r['candidates']}" + ("" if same else f" (default {name(d)})")
 
 
 def summary(r: dict) -> dict:
