@@ -525,6 +525,20 @@ struct DenseLoad {
       return __byte_perm(h, 0, 0x4140);  // two bytes into two 16-bit halves
     }
   }
+  // words WORD and WORD + 1 by one read: the sliding network asks for pairs
+  // that start on an 8-byte (u16) or 4-byte (u8) boundary of the stage
+  template <int ROW, int WORD>
+  __device__ __forceinline__ void get2(uint32_t &a, uint32_t &b) const {
+    if constexpr (sizeof(T) == 2) {
+      const uint2 t = *reinterpret_cast<const uint2 *>(base + ROW * BW + 2 * WORD);
+      a = t.x;
+      b = t.y;
+    } else {
+      const uint32_t t = *reinterpret_cast<const uint32_t *>(base + ROW * BW + 2 * WORD);
+      a = __byte_perm(t, 0, 0x4140);
+      b = __byte_perm(t, 0, 0x4342);
+    }
+  }
 };
 
 template <typename T, int K, bool COUNT, int MODE>
@@ -568,6 +582,53 @@ struct DenseEmit {
   }
 };
 
+// The item's results, turned back into rows (byte permutes) and stored
+// straight to the frame: 16-byte (u16) or 8-byte (u8) stores where the whole
+// eight columns are in the frame and the frame allows vector stores.
+template <typename T, int NO>
+__device__ __forceinline__ void dense_store_item(unsigned char *out, long long pitch, int x0, int y0, int tx, int ty,
+                                                 const uint32_t (&res)[NO], int tw_valid, int th_valid, bool vec_ok) {
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    if (ty + o < th_valid) {
+#pragma unroll
+      for (int g = 0; g < NO / 8; ++g) {
+        uint32_t rw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          rw[q] = __byte_perm(res[8 * g + 2 * q], res[8 * g + 2 * q + 1], o ? 0x7632 : 0x5410);
+        const int cx = tx + 8 * g;
+        T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + cx;
+        if (vec_ok && cx + 8 <= tw_valid) {
+          store_row8<T>(dst, rw);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (cx + q < tw_valid) dst[q] = static_cast<T>((rw[q >> 1] >> (16 * (q & 1))) & 0xffffu);
+        }
+      }
+    }
+  }
+}
+
+// The directional detector's signal bits of an item's two rows (stage rows
+// ty + R and ty + R + 1), eight columns at a time.
+template <typename T, int K, int NO>
+__device__ __forceinline__ void dense_item_dsig(const T *item, int BW, uint32_t (&dsig)[2][NO / 2],
+                                                const PackedOp op) {
+  constexpr int R = (K - 1) / 2;
+#pragma unroll
+  for (int g = 0; g < NO / 8; ++g) {
+    uint32_t e[4][6];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load_row8<T>(item + (R - 1 + q) * BW + 8 * g, e[q]);
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) dsig[o][4 * g + pp] = directional_sig(e[o], e[o + 1], e[o + 2], pp, op);
+  }
+}
+
 template <typename T, int K, bool COUNT, int MODE>
 __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, int BW, int r0, int SR, int seg_shift,
                                 int tw_valid, int th_valid, bool vec_ok, int lane, int &flagged, const PackedOp op) {
@@ -576,52 +637,54 @@ __device__ void dense_sep_strip(const T *S, const FrameDev *f, int x0, int y0, i
   constexpr int XOFF = xoff_for(R, sizeof(T));
   constexpr int NO = Net::kOut;  // output columns per item (a multiple of 8)
   static_assert(Net::kRows == K + 1 && NO % 8 == 0 && NO == dense_item_cols(ALGO_DENSE, K), "network shape");
-  // items: (row pair, NO-column segment); seg_shift = log2(tile_w / NO)
-  const int items = (SR >> 1) << seg_shift;
-  const int seg_mask = (1 << seg_shift) - 1;
+  static_assert(Net::kSliding == dense_sliding(K), "network form");
   unsigned char *const out = f->out;
   const long long pitch = f->out_pitch;
-  for (int it = lane; it < items; it += 32) {
-    const int sx = it & seg_mask, ry = it >> seg_shift;
-    const int tx = sx * NO, ty = r0 + (ry << 1);
-    const T *const item = S + ty * BW + XOFF + tx;  // stage row ty, output column x0
-    uint32_t dsig[2][NO / 2] = {};
-    if constexpr (MODE == kModeDirectional) {
-      // the line test on rows y (stage row ty + R) and y + 1, eight columns at a time
-#pragma unroll
-      for (int g = 0; g < NO / 8; ++g) {
-        uint32_t e[4][6];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) load_row8<T>(item + (R - 1 + q) * BW + 8 * g, e[q]);
-#pragma unroll
-        for (int o = 0; o < 2; ++o)
-#pragma unroll
-          for (int pp = 0; pp < 4; ++pp) dsig[o][4 * g + pp] = directional_sig(e[o], e[o + 1], e[o + 2], pp, op);
+  if constexpr (Net::kSliding) {
+    // A lane takes a span of 2^span_shift neighbouring items of one row
+    // pair, as many as spread the strip's items over the 32 lanes: the
+    // span's first item starts from its carry (Net::pre), and every item
+    // hands its carry (sorted columns and merged blocks that the next item's
+    // windows share) on. Neighbouring lanes take neighbouring row pairs of
+    // the same span column: the stage row pitch is an odd number of 16-byte
+    // units, so their reads spread over the banks (lanes of one row pair
+    // would be a span apart, in a few banks).
+    const int pairs = SR >> 1;
+    const int span_shift = min(seg_shift, max(0, seg_shift + (31 - __clz(pairs)) - 5));
+    const int units = pairs << (seg_shift - span_shift);
+    for (int u = lane; u < units; u += 32) {
+      const int ry = u % pairs, sp = u / pairs;
+      const int ty = r0 + (ry << 1);
+      const T *const row = S + ty * BW + XOFF;  // stage row ty, output column x0
+      int tx = sp * (NO << span_shift);
+      uint32_t carry[Net::kCarry];
+      Net::pre(DenseOp<K>{op}, DenseLoad<T, K>{row + tx + Net::kFirstCol, BW}, carry);
+#pragma unroll 1
+      for (int s = 0; s < (1 << span_shift); ++s, tx += NO) {
+        const T *const item = row + tx;
+        uint32_t dsig[2][NO / 2] = {};
+        if constexpr (MODE == kModeDirectional) dense_item_dsig<T, K, NO>(item, BW, dsig, op);
+        uint32_t res[NO];
+        Net::body(DenseOp<K>{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
+                  DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged},
+                  carry);
+        dense_store_item<T, NO>(out, pitch, x0, y0, tx, ty, res, tw_valid, th_valid, vec_ok);
       }
     }
-    uint32_t res[NO];
-    Net::run(DenseOp<K>{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
-             DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
-#pragma unroll
-    for (int o = 0; o < 2; ++o) {
-      if (ty + o < th_valid) {
-#pragma unroll
-        for (int g = 0; g < NO / 8; ++g) {
-          uint32_t row[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            row[q] = __byte_perm(res[8 * g + 2 * q], res[8 * g + 2 * q + 1], o ? 0x7632 : 0x5410);
-          const int cx = tx + 8 * g;
-          T *dst = reinterpret_cast<T *>(out + (long long)(y0 + ty + o) * pitch) + x0 + cx;
-          if (vec_ok && cx + 8 <= tw_valid) {
-            store_row8<T>(dst, row);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (cx + q < tw_valid) dst[q] = static_cast<T>((row[q >> 1] >> (16 * (q & 1))) & 0xffffu);
-          }
-        }
-      }
+  } else {
+    // items: (row pair, NO-column segment), one at a time; seg_shift = log2(tile_w / NO)
+    const int items = (SR >> 1) << seg_shift;
+    const int seg_mask = (1 << seg_shift) - 1;
+    for (int it = lane; it < items; it += 32) {
+      const int sx = it & seg_mask, ry = it >> seg_shift;
+      const int tx = sx * NO, ty = r0 + (ry << 1);
+      const T *const item = S + ty * BW + XOFF + tx;  // stage row ty, output column x0
+      uint32_t dsig[2][NO / 2] = {};
+      if constexpr (MODE == kModeDirectional) dense_item_dsig<T, K, NO>(item, BW, dsig, op);
+      uint32_t res[NO];
+      Net::run(DenseOp<K>{op}, DenseLoad<T, K>{item + Net::kFirstCol, BW},
+               DenseEmit<T, K, COUNT, MODE>{item + R * BW, BW, dsig, res, op, tx, ty, tw_valid, th_valid, flagged});
+      dense_store_item<T, NO>(out, pitch, x0, y0, tx, ty, res, tw_valid, th_valid, vec_ok);
     }
   }
 }

@@ -23,6 +23,10 @@ __host__ __device__ constexpr bool dense_algo(int algo) { return algo == ALGO_DE
 // this many columns): 8 for the 3x3 path; for the separable networks the
 // generator's choice (fnr_separable.cuh, SepNet<K>::kOut), repeated here for
 // the host's tile checks.
+// Whether a lane of the dense strategy filters a span of neighbouring items,
+// handing the sorted columns and merged blocks they share from item to item
+// (the 7x7 network), rather than each item on its own (5x5).
+__host__ __device__ constexpr bool dense_sliding(int k) { return k == 7; }
 __host__ __device__ constexpr int dense_item_cols(int algo, int k) {
   return algo == ALGO_DENSE && k == 7 ? 8 : 8;
 }
@@ -157,6 +161,10 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   L.r = (k - 1) / 2;
   const int xoff = xoff_for(L.r, esize);
   L.bw = tile_w + 2 * xoff;
+  // the sliding dense items: a row pitch of an odd number of 16-byte units
+  // (the box reads a few more columns), so that lanes reading the same column
+  // of neighbouring row pairs fall in different banks
+  if (algo == ALGO_DENSE && dense_sliding(k) && ((L.bw * esize / 16) & 1) == 0) L.bw += 16 / esize;
   L.bh = tile_h + 2 * L.r;
   L.vw = tile_w + 2 * L.r;
   // pair words cover stage columns [cb, cb + 2 np): every column a window reads

@@ -54,6 +54,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(HERE, "fnr_separable.cuh")
 KS = (5, 7)
 NOUT = {5: 8, 7: 8}   # output columns per lane item
+# word columns an item of the sliding form sorts beyond its own windows, for
+# the next item: they put each item's new word columns on an 8-byte boundary
+# of the stage (two words per shared load)
+LOOKAHEAD = {5: 1, 7: 0}
+# windows whose kernel runs the sliding form (a lane filters a span of items
+# and hands the shared columns and blocks on); the others run items on their
+# own (the 5x5 sliding form measured slower: its carry spills at the
+# 96-register cap of two CTAs per SM)
+SLIDING = {5: False, 7: True}
 NEG, POS = "-inf", "+inf"
 
 # optimal-size sorting networks for small n (D. Knuth, TAOCP 5.3.4)
@@ -228,9 +237,10 @@ def words_per_row(k: int) -> int:
     return (NOUT[k] - 1 + R - first_word_col(k)) // 2 + 1
 
 
-def horizontal(p: Prog, col, k: int):
+def horizontal(p: Prog, col, k: int, x0: int = 0):
     """col(c) -> the sorted column c (k row-packed values). Returns, per output
-    column j, (j, median, window min, window max)."""
+    column j of the item whose first output column is x0, (j, median, window
+    min, window max)."""
     m = (k * k - 1) // 2
     M2: Dict[int, List[int]] = {}
 
@@ -242,7 +252,7 @@ def horizontal(p: Prog, col, k: int):
 
     outs = []
     if k == 5:
-        for x in range(0, NOUT[k], 2):
+        for x in range(x0, x0 + NOUT[k], 2):
             A, B = m2(x - 1), m2(x + 1)             # columns x-1 .. x+2, shared by x and x+1
             S = merge(p, A, B, range(m - k, m + 1))
             smin, smax = p.mn(A[0], B[0]), p.mx(A[-1], B[-1])
@@ -257,7 +267,7 @@ def horizontal(p: Prog, col, k: int):
                 B4[j] = (merge(p, A, B, range(3, 25)), p.mn(A[0], B[0]), p.mx(A[-1], B[-1]))
             return B4[j]
 
-        for x in range(0, NOUT[k], 2):               # columns x-2 .. x+3, shared by x and x+1
+        for x in range(x0, x0 + NOUT[k], 2):         # columns x-2 .. x+3, shared by x and x+1
             if x % 4 == 0:
                 (Bd, bmin, bmax), A = b4(x), m2(x - 2)
             else:
@@ -272,11 +282,11 @@ def horizontal(p: Prog, col, k: int):
     return outs
 
 
-def item_program(k: int):
-    """The whole lane item: inputs r[row][word] (x-packed), outputs per column."""
-    p = Prog()
+def _columns(p: Prog, k: int, w_first: int, w_end: int):
+    """col(c) for the word columns w_first .. w_end-1 (word w: columns
+    first_word_col(k) + 2w and the next), built on first use: the rows of a
+    word column are loaded, sorted vertically and transposed."""
     w0 = first_word_col(k)
-    nw = words_per_row(k)
     cols: Dict[int, List[int]] = {}
     loaded: Dict[int, List[int]] = {}
 
@@ -291,16 +301,107 @@ def item_program(k: int):
             # use: few inputs are live at a time, and the loads' latency
             # overlaps the previous column's work
             w = (c - w0) // 2
+            assert w_first <= w < w_end, (c, w)
             rows = rows_of(w)
-            if w + 1 < nw:
+            if w + 1 < w_end:
                 rows_of(w + 1)
             top, bot = vertical(p, rows, k)
             cols[w0 + 2 * w] = [p.lo(top[i], bot[i]) for i in range(k)]
             cols[w0 + 2 * w + 1] = [p.hi(top[i], bot[i]) for i in range(k)]
         return cols[c]
 
-    outs = horizontal(p, col, k)
+    return col
+
+
+def item_program(k: int):
+    """The whole lane item: inputs r[row][word] (x-packed), outputs per column."""
+    p = Prog()
+    outs = horizontal(p, _columns(p, k, 0, words_per_row(k)), k)
     return p, outs
+
+
+def _ancestors(p: Prog, roots) -> set:
+    seen = set(roots)
+    for d, kind, args in reversed(p.ops):
+        if d in seen and kind != "in":
+            seen |= {a for a in args if isinstance(a, int)}
+    return seen
+
+
+def span_program(k: int):
+    """The sliding form of the item, for a lane that filters several items of
+    one row pair side by side. Neighbouring items (x0 - NOUT, x0) share sorted
+    columns and merged blocks: the program of both is built, the values of the
+    left item that the right one reads are its carry, and
+      pre  computes the carry of the item at x0 (what the item at x0 - NOUT
+           would hand over) from the words they share,
+      body computes the item at x0 from its carry and its new word columns and
+           leaves the carry of the item at x0 + NOUT (the same values NOUT
+           columns further right, matched by their structure).
+    Returns (p, pre ops, body ops, carry in, carry out, outputs of x0)."""
+    n = NOUT[k]
+    shift = n // 2                                  # words per item
+    nw = words_per_row(k)
+    w0 = first_word_col(k)
+    p = Prog()
+    col = _columns(p, k, -shift, nw + LOOKAHEAD[k])
+    outs_a = horizontal(p, col, k, -n)
+    ahead_a = [v for j in range(LOOKAHEAD[k]) for h in (0, 1) for v in col(w0 + 2 * (nw + j - shift) + h)]
+    outs_b = horizontal(p, col, k, 0)
+    ahead_b = [v for j in range(LOOKAHEAD[k]) for h in (0, 1) for v in col(w0 + 2 * (nw + j) + h)]
+    da = _ancestors(p, [v for o in outs_a for v in o[1:]] + ahead_a)
+    db = _ancestors(p, [v for o in outs_b for v in o[1:]] + ahead_b)
+    out_b = {v for o in outs_b for v in o[1:]}
+
+    def cut(left, roots):
+        """Body ops and carry when the values in `left` come from the left item."""
+        ops = [op for op in p.ops if op[0] in roots and op[0] not in left]
+        need = {a for _, kind, args in ops if kind != "in" for a in args if a in left} | (out_b & left)
+        return ops, sorted(need)
+    left = set(da)
+    body, carry_in = cut(left, db)
+    # structural keys: equal keys compute the same function of the same words
+    intern: Dict[tuple, int] = {}
+    key: Dict[int, int] = {}
+    for d, kind, args in p.ops:
+        if kind == "in":
+            t = ("in", *args[0])
+        else:
+            ka = [key[a] for a in args]
+            t = (kind, *(sorted(ka) if kind in ("min", "max") else ka))
+        key[d] = intern.setdefault(t, len(intern))
+    moved: Dict[int, object] = {}                    # key of the same structure `shift` words right
+    for d, kind, args in p.ops:
+        if kind == "in":
+            row, w = args[0]
+            tm = ("in", row, w + shift)
+        else:
+            km = [moved[a] for a in args]
+            tm = None if None in km else (kind, *(sorted(km) if kind in ("min", "max") else km))
+        moved[d] = intern.get(tm) if tm is not None else None
+    by_key = {key[d]: d for d in key}
+    # A transposition whose inputs the left item holds is moved to the left
+    # item (whose own word columns' transpositions then compute it one item
+    # earlier) when that shrinks the carry: one transposed value instead of
+    # the two sorted words it reads.
+    for d, kind, args in list(body):
+        if kind in ("lo", "hi") and all(a in left for a in args) and moved[d] in by_key:
+            twin = by_key[moved[d]]
+            trial = left | {d}
+            db_t = db | _ancestors(p, [twin])
+            ops_t, need_t = cut(trial, db_t)
+            if len(need_t) < len(carry_in):
+                left, db = trial, db_t
+                body, carry_in = ops_t, need_t
+    carry_out = []
+    for c in carry_in:
+        assert moved[c] is not None and moved[c] in by_key, ("carry without a counterpart", c)
+        d = by_key[moved[c]]
+        assert d in db and d not in left, ("carry counterpart outside the item", c, d)
+        carry_out.append(d)
+    pre_set = _ancestors(p, carry_in)
+    pre = [op for op in p.ops if op[0] in pre_set]
+    return p, pre, body, carry_in, carry_out, outs_b
 
 
 def horizontal_program(k: int):
@@ -346,11 +447,9 @@ def op_counts(ops) -> Dict[str, int]:
 # ---------------------------------------------------------------------------
 # emission
 # ---------------------------------------------------------------------------
-def emit_item(k: int) -> List[str]:
-    p, outs = item_program(k)
-    ops = live_ops(p, outs)
-    c = op_counts(ops)
-    # min and max of the same operands form a compare-exchange
+def _emit_ops(k: int, ops, outs, lines: List[str], indent: str = "    ", pairs: bool = True) -> None:
+    """Emit a straight-line op list; a min and max of the same operands form a
+    compare-exchange whose max may take the FMA-pipe form (op.cmax<J>)."""
     pair_of = {}
     mins = {}
     for d, kind, args in ops:
@@ -358,47 +457,105 @@ def emit_item(k: int) -> List[str]:
             mins[tuple(sorted(args))] = d
         elif kind == "max" and tuple(sorted(args)) in mins:
             pair_of[d] = mins[tuple(sorted(args))]
-    emit_of = {o[0]: o for o in outs}
-    last_use = {}
-    for d, kind, args in ops:
-        for a in args:
-            if isinstance(a, int):
-                last_use[a] = d
-    done_at = {}
+    defined = {d for d, _, _ in ops}
+    done_at: Dict[int, list] = {}
     for o in outs:
-        done_at.setdefault(max(o[1:]), []).append(o)
-    nw = words_per_row(k)
+        done_at.setdefault(max(v for v in o[1:] if v in defined) if any(v in defined for v in o[1:]) else -1,
+                           []).append(o)
+    for o in sorted(done_at.pop(-1, []), key=lambda o: o[0]):
+        lines.append(f"{indent}emit.template put<{o[0]}>(v{o[1]}, v{o[2]}, v{o[3]});")
+    # words (w, w + 1) of a row that start on an 8-byte boundary of the stage
+    # (w of parity `par`) are read by one shared load where both are read
+    par = (-first_word_col(k) // 2) % 2
+    word_at = {args[0]: d for d, kind, args in ops if kind == "in"}
+    loaded = set()
+    j = 0
+    for d, kind, args in ops:
+        if kind == "in":
+            if d in loaded:
+                continue
+            row, word = args[0]
+            base = word if word % 2 == par else word - 1
+            mate = word_at.get((row, base + 1 if word == base else base)) if pairs else None
+            if mate is None:
+                lines.append(f"{indent}const uint32_t v{d} = ld.template get<{row}, {word}>();")
+            else:
+                lo_v, hi_v = (d, mate) if word == base else (mate, d)
+                lines.append(f"{indent}uint32_t v{lo_v}, v{hi_v};")
+                lines.append(f"{indent}ld.template get2<{row}, {base}>(v{lo_v}, v{hi_v});")
+                loaded.add(mate)
+        elif kind == "min":
+            lines.append(f"{indent}const uint32_t v{d} = op.mn(v{args[0]}, v{args[1]});")
+        elif kind == "max":
+            if d in pair_of:
+                lines.append(f"{indent}const uint32_t v{d} = op.template cmax<{j}>(v{args[0]}, v{args[1]}, "
+                             f"v{pair_of[d]});")
+                j += 1
+            else:
+                lines.append(f"{indent}const uint32_t v{d} = op.mx(v{args[0]}, v{args[1]});")
+        elif kind == "lo":
+            lines.append(f"{indent}const uint32_t v{d} = __byte_perm(v{args[0]}, v{args[1]}, 0x5410);")
+        elif kind == "hi":
+            lines.append(f"{indent}const uint32_t v{d} = __byte_perm(v{args[0]}, v{args[1]}, 0x7632);")
+        for o in sorted(done_at.get(d, []), key=lambda o: o[0]):
+            lines.append(f"{indent}emit.template put<{o[0]}>(v{o[1]}, v{o[2]}, v{o[3]});")
+
+
+def _shape(k: int, sliding: bool) -> List[str]:
+    return [f"template <> struct SepNet<{k}> {{",
+            f"  static constexpr bool kSliding = {'true' if sliding else 'false'};",
+            f"  static constexpr int kOut = {NOUT[k]};",
+            f"  static constexpr int kRows = {k + 1};",
+            f"  static constexpr int kWords = {words_per_row(k)};",
+            f"  static constexpr int kFirstCol = {first_word_col(k)};"]
+
+
+def emit_item(k: int) -> List[str]:
+    p, outs = item_program(k)
+    ops = live_ops(p, outs)
+    c = op_counts(ops)
     lines = [f"// k={k}: {c.get('min', 0)} min, {c.get('max', 0)} max, {c.get('lo', 0) + c.get('hi', 0)} permutes"
-             f" per item of {2 * NOUT[k]} pixels",
-             f"template <> struct SepNet<{k}> {{",
-             f"  static constexpr int kOut = {NOUT[k]};",
-             f"  static constexpr int kRows = {k + 1};",
-             f"  static constexpr int kWords = {nw};",
-             f"  static constexpr int kFirstCol = {first_word_col(k)};",
+             f" per item of {2 * NOUT[k]} pixels"] + _shape(k, False) + [
              "  // ld.get<row, word>(): x-packed word `word` (columns x0 + kFirstCol + 2 word and the next)",
              "  // of stage row `row` of the item (0 .. k); emit.put<j>(g_m, g_min, g_max) gets the",
              "  // row-packed results of output column x0 + j (low half row y, high half row y + 1)",
              "  template <class Op, class Load, class Emit>",
              "  __device__ __forceinline__ static void run(const Op op, Load &&ld, Emit &&emit) {"]
-    j = 0
-    for d, kind, args in ops:
-        if kind == "in":
-            row, word = args[0]
-            lines.append(f"    const uint32_t v{d} = ld.template get<{row}, {word}>();")
-        elif kind == "min":
-            lines.append(f"    const uint32_t v{d} = op.mn(v{args[0]}, v{args[1]});")
-        elif kind == "max":
-            if d in pair_of:
-                lines.append(f"    const uint32_t v{d} = op.template cmax<{j}>(v{args[0]}, v{args[1]}, v{pair_of[d]});")
-                j += 1
-            else:
-                lines.append(f"    const uint32_t v{d} = op.mx(v{args[0]}, v{args[1]});")
-        elif kind == "lo":
-            lines.append(f"    const uint32_t v{d} = __byte_perm(v{args[0]}, v{args[1]}, 0x5410);")
-        elif kind == "hi":
-            lines.append(f"    const uint32_t v{d} = __byte_perm(v{args[0]}, v{args[1]}, 0x7632);")
-        for o in sorted(done_at.get(d, []), key=lambda o: o[0]):
-            lines.append(f"    emit.template put<{o[0]}>(v{o[1]}, v{o[2]}, v{o[3]});")
+    _emit_ops(k, ops, outs, lines, pairs=False)
+    lines += ["  }", "};", ""]
+    return lines
+
+
+def emit_sliding(k: int) -> List[str]:
+    p, pre, body, carry_in, carry_out, outs = span_program(k)
+    c = op_counts(body)
+    cp = op_counts(pre)
+    nc = len(carry_in)
+    lines = [f"// k={k}, sliding items of {2 * NOUT[k]} pixels: per item {c.get('min', 0)} min, {c.get('max', 0)} max,"
+             f" {c.get('lo', 0) + c.get('hi', 0)} permutes and {c.get('in', 0)} word loads, {nc} values"
+             f" carried; before a lane's first item {cp.get('min', 0) + cp.get('max', 0)} min/max,"
+             f" {cp.get('lo', 0) + cp.get('hi', 0)} permutes"] + _shape(k, True) + [
+             f"  static constexpr int kCarry = {nc};",
+             "  // ld.get<row, word>(): x-packed word `word` (columns x0 + kFirstCol + 2 word and the next)",
+             "  // of stage row `row` of the item at x0 (0 .. k); ld.get2<row, word>(a, b): words `word` and",
+             "  // `word` + 1 by one 8-byte aligned read; emit.put<j>(g_m, g_min, g_max) gets the",
+             "  // row-packed results of output column x0 + j (low half row y, high half row y + 1)",
+             "  // pre: the carry of the item at x0, from its first word columns",
+             "  template <class Op, class Load>",
+             f"  __device__ __forceinline__ static void pre(const Op op, Load &&ld, uint32_t (&c)[{nc}]) {{"]
+    _emit_ops(k, pre, [], lines)
+    for i, d in enumerate(carry_in):
+        lines.append(f"    c[{i}] = v{d};")
+    lines += ["  }",
+              "  // body: the item at x0 from its carry c; leaves in c the carry of the item at x0 + kOut",
+              "  template <class Op, class Load, class Emit>",
+              f"  __device__ __forceinline__ static void body(const Op op, Load &&ld, Emit &&emit, "
+              f"uint32_t (&c)[{nc}]) {{"]
+    for i, d in enumerate(carry_in):
+        lines.append(f"    const uint32_t v{d} = c[{i}];")
+    _emit_ops(k, body, outs, lines)
+    for i, d in enumerate(carry_out):
+        lines.append(f"    c[{i}] = v{d};")
     lines += ["  }", "};", ""]
     return lines
 
@@ -416,7 +573,7 @@ def emit() -> str:
         "",
     ]
     for k in KS:
-        lines += emit_item(k)
+        lines += emit_sliding(k) if SLIDING[k] else emit_item(k)
     lines += ["}  // namespace fnr", ""]
     return "\n".join(lines)
 
@@ -447,11 +604,17 @@ def main() -> None:
     with open(HEADER, "w") as fh:
         fh.write(emit())
     for k in KS:
-        p, outs = item_program(k)
-        c = op_counts(live_ops(p, outs))
+        if SLIDING[k]:
+            _, pre, body, carry_in, _, _ = span_program(k)
+            c = op_counts(body)
+            what = f"per sliding item, {len(carry_in)} values carried"
+        else:
+            p, outs = item_program(k)
+            c = op_counts(live_ops(p, outs))
+            what = "per item"
         mm = c.get("min", 0) + c.get("max", 0)
-        print(f"k={k}: {mm} min/max ({mm / (2 * NOUT[k]):.1f} per pixel), "
-              f"{c.get('lo', 0) + c.get('hi', 0)} permutes per item")
+        print(f"k={k}: {mm} min/max {what} ({mm / (2 * NOUT[k]):.2f} per pixel), "
+              f"{c.get('lo', 0) + c.get('hi', 0)} permutes")
 
 
 if __name__ == "__main__":

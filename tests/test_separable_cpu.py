@@ -10,6 +10,8 @@ the CPU before any kernel runs them.
   vertical stage hands over;
 * the whole lane item (vertical, transpose, horizontal, on packed pairs of
   16-bit lanes) against numpy's sort on random and tie-heavy values;
+* the sliding form the 7x7 kernel runs (a carry of shared sorted columns and
+  merged blocks handed from item to item) the same way, over four items;
 * the generated header is the generator's current output.
 """
 import os
@@ -139,6 +141,87 @@ def test_item_random_values(k):
             assert np.array_equal((v[med] >> (16 * half)) & mask, srt[:, (k * k - 1) // 2]), (o, half)
             assert np.array_equal((v[gmn] >> (16 * half)) & mask, srt[:, 0])
             assert np.array_equal((v[gmx] >> (16 * half)) & mask, srt[:, -1])
+
+
+@pytest.mark.parametrize("k", KS)
+def test_span_random_values(k):
+    """The sliding form (pre, then body item after item with the carry handed
+    on) against numpy's sort for every window of four items. The kernel runs
+    it for the windows gs.SLIDING names; the others are checked too."""
+    p, pre, body, carry_in, carry_out, outs = gs.span_program(k)
+    assert len(carry_in) == len(carry_out)
+    R = (k - 1) // 2
+    n = gs.NOUT[k]
+    w0 = gs.first_word_col(k)
+    nw = gs.words_per_row(k)
+    items = 4
+    rng = np.random.default_rng(100 + k)
+    trials = 64
+    mask = np.uint32(0xFFFF)
+
+    def lane_min(a, b):
+        return np.minimum(a & mask, b & mask) | (np.minimum(a >> 16, b >> 16) << 16)
+
+    def lane_max(a, b):
+        return np.maximum(a & mask, b & mask) | (np.maximum(a >> 16, b >> 16) << 16)
+
+    def lo(a, b):
+        return (a & mask) | ((b & mask) << 16)
+
+    def hi(a, b):
+        return (a >> 16) | ((b >> 16) << 16)
+    width = n * (items - 1) + 2 * (nw + gs.LOOKAHEAD[k])  # image column 0 = x0 + w0 of the first item
+    imgs = np.stack([rng.integers(0, [2, 6, 300, 65536][t % 4], size=(k + 1, width)).astype(np.uint32)
+                     for t in range(trials)])
+
+    def words(ops, x):
+        got = {}
+        for d, kind, args in ops:
+            if kind == "in":
+                r, w = args[0]
+                c = x + 2 * w
+                got[d] = imgs[:, r, c] | (imgs[:, r, c + 1] << 16)
+        return got
+    v = gs.evaluate(pre, words(pre, 0), lane_min, lane_max, lo, hi)
+    carry = [v[d] for d in carry_in]
+    for it in range(items):
+        inputs = words(body, it * n)
+        inputs.update(zip(carry_in, carry))
+        v = gs.evaluate(body, inputs, lane_min, lane_max, lo, hi)
+        carry = [v[d] for d in carry_out]
+        for o, med, gmn, gmx in outs:
+            c0 = it * n + o - R - w0                 # first window column in the image
+            for half in (0, 1):
+                win = imgs[:, half:half + k, c0:c0 + k].reshape(trials, -1)
+                srt = np.sort(win, axis=1)
+                assert np.array_equal((v[med] >> (16 * half)) & mask, srt[:, (k * k - 1) // 2]), (it, o, half)
+                assert np.array_equal((v[gmn] >> (16 * half)) & mask, srt[:, 0]), (it, o, half)
+                assert np.array_equal((v[gmx] >> (16 * half)) & mask, srt[:, -1]), (it, o, half)
+
+
+def test_span_op_counts_recorded():
+    """Per sliding item of 16 pixels: 456 (5x5) and 964 (7x7) min/max
+    operations, against 534 and 1240 for an item computed on its own."""
+    for k, want in ((5, 456), (7, 964)):
+        _, _, body, _, _, _ = gs.span_program(k)
+        c = gs.op_counts(body)
+        assert c["min"] + c["max"] == want
+
+
+def test_header_forms_match_kernel_choice():
+    """The header holds the sliding form exactly for the windows the kernel's
+    dense_sliding() names (k = 7), the single-item form for the others."""
+    with open(gs.HEADER) as fh:
+        text = fh.read()
+    for k in KS:
+        block = text[text.index(f"struct SepNet<{k}>"):]
+        block = block[:block.index("};")]
+        assert (f"kSliding = {'true' if gs.SLIDING[k] else 'false'}") in block
+        assert ("static void body(" in block) == gs.SLIDING[k]
+        assert ("static void run(" in block) == (not gs.SLIDING[k])
+    params = open(os.path.join(ROOT, "paper_1201_3972_gb300", "csrc", "fnr_params.h")).read()
+    assert "constexpr bool dense_sliding(int k) { return k == 7; }" in params
+    assert [k for k in KS if gs.SLIDING[k]] == [7]
 
 
 def test_op_counts_recorded():
