@@ -350,12 +350,13 @@ struct PackedOp {
 // min/max, so the ALU pipe bounds them: of every kPeriod exchanges, kAlu take
 // the ALU max and the others the FMA-pipe form. Measured on GB300 (640x512
 // sweep, 128 frames per class): k = 5 with 1 of 8 on the ALU 0.0968 ms
-// against 0.1029 with 2 of 5 (eight consumer warps per SM at two CTAs); k = 7,
-// whose registers allow one CTA per SM, 0.1933 ms with 2 of 5 against 0.1971
-// with 1 of 8 (fewer warps to hide the longer multiply-add chain).
+// against 0.1029 with 2 of 5 (eight consumer warps per SM at two CTAs); k = 7
+// (sliding items, one CTA per SM) 0.1685 ms with 1 of 3 against 0.1704 with
+// 2 of 5, 0.1688 with 3 of 10, 0.1706 with 2 of 7, 0.1746 with 1 of 5 and
+// 0.1725 with 1 of 2.
 template <int K>
 struct DenseOp : PackedOp {
-  static constexpr int kPeriod = K == 5 ? 8 : 5, kAlu = K == 5 ? 1 : 2;
+  static constexpr int kPeriod = K == 5 ? 8 : 3, kAlu = K == 5 ? 1 : 1;
   template <int J>
   __device__ __forceinline__ uint32_t cmax(uint32_t a, uint32_t b, uint32_t lo) const {
     if (J % kPeriod < kAlu) return vmax2(a, b);
