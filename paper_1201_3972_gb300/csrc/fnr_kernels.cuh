@@ -958,6 +958,8 @@ __device__ __forceinline__ void median_pair(const T *S, T *O, int TW, int BW, in
                                             PackedOp op) {
   constexpr int R = (K - 1) / 2;
   constexpr int XOFF = xoff_for(R, sizeof(T));
+  // only the two output offsets stay live across the network
+  const int oa = ya * TW + xa, ob = yb * TW + xb;
   uint32_t v[K * K];
   if constexpr (sizeof(T) == 2) {
     const uint32_t *W32 = reinterpret_cast<const uint32_t *>(S);
@@ -1016,8 +1018,8 @@ __device__ __forceinline__ void median_pair(const T *S, T *O, int TW, int BW, in
     }
   }
   const uint32_t m = MedianNet<K>::run(v, op);
-  O[ya * TW + xa] = static_cast<T>(m & 0xffffu);
-  O[yb * TW + xb] = static_cast<T>(m >> 16);
+  O[oa] = static_cast<T>(m & 0xffffu);
+  O[ob] = static_cast<T>(m >> 16);
 }
 
 // The flagged pixels of the warp's strip, two per lane.
@@ -1072,56 +1074,59 @@ __device__ void network_pooled(const T *S, T *O, const unsigned char *warp_block
   }
 }
 
+// Transpose of the 32x32 bit matrix whose row l is lane l's word: afterwards
+// lane j holds the word whose bit l is bit j of lane l's word. Five rounds
+// of one shuffle each swap the off-diagonal blocks of halving size (16, 8,
+// 4, 2, 1) between lane pairs l, l ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
+  constexpr uint32_t kMask[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const int s = 16 >> i;
+    const uint32_t m = kMask[i];
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, s);
+    x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y << s) & ~m));
+  }
+  return x;
+}
+
 // Bit planes of the stage rows [r0, r0 + rows): word (bit b, row i, column
 // word w) at planes[(b * rows + i) * PW + w] holds bit b of the 32 pixels of
 // row r0 + i from column 32w. This order keeps the selection's reads, where
-// each lane reads its own pixel's rows at one bit, in distinct banks. One
-// ballot per (row, word, bit); the ballots of kPlaneGroup items go through
-// the warp's staging buffer (lane 0 writes them as 16-byte vectors, then
-// every lane moves two words into place). The last word of every row is zero
-// (a window segment may reach into it). Returns the OR of the pixels.
+// each lane reads its own pixel's rows at one bit, in distinct banks. Lane l
+// packs the pixels of column 32w + l of 32 / NB consecutive rows (2 of 16
+// bits, 4 of 8 bits) into one word; one warp transpose turns the 32 words
+// into the 32 plane words of those rows (lane q * NB + b: bit b of the
+// group's row q), each stored by its lane. The last word of every row is
+// zero (a window segment may reach into it). Returns the OR of the pixels.
 template <typename T>
-__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, uint32_t *stage, int BW, int r0, int rows, int PW,
-                                      int lane) {
+__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int r0, int rows, int PW, int lane) {
   constexpr int NB = 8 * sizeof(T);
-  constexpr int G = kPlaneGroup;
+  constexpr int P = 32 / NB;  // rows per transpose
   const int wpr = PW - 1;
-  const int items = rows * wpr;
+  const int groups = (rows + P - 1) / P;
+  const int b = lane & (NB - 1), q = lane / NB;  // the plane word this lane holds after a transpose
   uint32_t orv = 0;
-  for (int it0 = 0; it0 < items; it0 += G) {
-    uint32_t v[G];
+  for (int it = 0; it < groups * wpr; ++it) {
+    const int g = it / wpr, w = it - g * wpr;
+    const int col = (w << 5) + lane;
+    uint32_t x = 0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const int it = it0 + g < items ? it0 + g : items - 1;  // a repeated item rewrites the same words
-      const int row = it / wpr, w = it - row * wpr;
-      const int col = (w << 5) + lane;
-      v[g] = col < BW ? static_cast<uint32_t>(S[(r0 + row) * BW + col]) : 0u;
-      orv |= v[g];
+    for (int j = 0; j < P; ++j) {
+      const int row = g * P + j;
+      const uint32_t px = (col < BW && row < rows) ? static_cast<uint32_t>(S[(r0 + row) * BW + col]) : 0u;
+      x |= px << (NB * j);
     }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      uint32_t bits[NB];
-#pragma unroll
-      for (int b = 0; b < NB; ++b) bits[b] = __ballot_sync(0xffffffffu, (v[g] >> b) & 1u);
-      if (lane == 0) {
-        uint4 *dst = reinterpret_cast<uint4 *>(stage + g * NB);
-#pragma unroll
-        for (int j = 0; j < NB / 4; ++j) dst[j] = make_uint4(bits[4 * j], bits[4 * j + 1], bits[4 * j + 2], bits[4 * j + 3]);
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int idx = lane; idx < G * NB; idx += 32) {
-      const int g = idx / NB, b = idx - g * NB;
-      const int it = it0 + g < items ? it0 + g : items - 1;
-      const int row = it / wpr, w = it - row * wpr;
-      planes[(b * rows + row) * PW + w] = stage[idx];
-    }
-    __syncwarp();
+    orv |= x;
+    x = warp_transpose32(x, lane);
+    const int row = g * P + q;
+    if (row < rows) planes[(b * rows + row) * PW + w] = x;
   }
   for (int it = lane; it < NB * rows; it += 32) planes[it * PW + wpr] = 0u;
   __syncwarp();
-  return __reduce_or_sync(0xffffffffu, orv);
+#pragma unroll
+  for (int j = 1; j < P; ++j) orv |= orv >> (NB * j);
+  return __reduce_or_sync(0xffffffffu, orv & ((1u << NB) - 1u));
 }
 
 // Flagged pixels of the strip: radix select on the window, most significant
@@ -1584,8 +1589,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
           radix_sparse_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {
           uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
-          uint32_t *pstage = reinterpret_cast<uint32_t *>(wbase + L.w_stage);
-          const uint32_t orv = build_planes_warp<T>(S, planes, pstage, BW, r0, L.plane_rows, L.pw, lane);
+          const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, lane);
           bitplane_strip<T, K>(planes, O, list, flagged, TW, L.plane_rows, L.pw, 32 - __clz(static_cast<int>(orv)),
                                r0, lane);
         }

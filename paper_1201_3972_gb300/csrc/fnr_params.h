@@ -99,7 +99,6 @@ __host__ __device__ constexpr int xoff_for(int r, int esize) {
 // ahead of the slowest consumer warp).
 __host__ __device__ constexpr int num_stages(int algo) { return dense_algo(algo) ? 3 : 2; }
 __host__ __device__ constexpr int out_buffers(int algo) { return algo == ALGO_BITPLANE ? 1 : 2; }
-constexpr int kPlaneGroup = 4;  // (row, word) items of a bit-plane build step
 // Whether the network strategy pools the flagged pixels of a tile across its
 // strips; a pooling warp keeps two flagged lists, alternating by tile, since
 // the other warps may still read its previous list while it builds the next.
@@ -147,7 +146,6 @@ struct Layout {
   int warp_bytes;      // size of one per-warp block
   int w_list, w_vmin, w_vmax, w_planes;  // offsets inside a per-warp block
   int list_bytes;                        // one flagged list (two when pooling, alternating by tile)
-  int w_stage;                           // bit-plane strategy: ballot staging for the plane build
   int plane_rows;      // rows of bit planes a warp builds (its strip + halo)
   int off_bar;         // full[stages], empty[stages]
   int off_sync;        // network strategy: pooled[stages] barriers (and a spare row), then list counts [stages][warps]
@@ -201,7 +199,7 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
     L.off_out[1] = off;
     off += outb;
   }
-  L.w_list = L.w_vmin = L.w_vmax = L.w_planes = L.w_stage = -1;
+  L.w_list = L.w_vmin = L.w_vmax = L.w_planes = -1;
   int w = 0;
   if (!dense_algo(algo)) {
     L.list_bytes = align_up(L.sr * tile_w * 2, 16);
@@ -211,12 +209,10 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
   }
   if (algo == ALGO_BITPLANE) {
     // the planes are built after the horizontal pass has consumed the extreme
-    // words, so they overlay them; the ballots of a few (row, word) items are
-    // staged in a small buffer of their own on the way
+    // words, so they overlay them
     const int planes = align_up(L.nbmax * L.plane_rows * L.pw * 4, 16);
     L.w_planes = L.w_vmin;
     if (L.w_planes + planes > w) w = L.w_planes + planes;
-    L.w_stage = w; w += kPlaneGroup * L.nbmax * 4;
   }
   L.warp_bytes = align_up(w, 128);
   L.off_warp = off; off += kConsumerWarps * L.warp_bytes;

@@ -236,9 +236,7 @@ int main() {
               if (overlap(L.w_list, list1, v0, v1) || v1 > L.warp_bytes) ++bad;
               if (algo == ALGO_BITPLANE) {
                 const long p1 = L.w_planes + (long)L.nbmax * L.plane_rows * L.pw * 4;
-                const long s0 = L.w_stage, s1 = L.w_stage + (long)kPlaneGroup * L.nbmax * 4;
                 if (overlap(L.w_list, list1, L.w_planes, p1) || p1 > L.warp_bytes) ++bad;
-                if (overlap(s0, s1, L.w_list, list1) || overlap(s0, s1, L.w_planes, p1) || s1 > L.warp_bytes || s0 % 16) ++bad;
               }
             }
           }
