@@ -46,6 +46,9 @@ def test_noalloc_matches_run_on_two_calls_in_a_row():
             (synth.workload_sweep_u14()[4].make(), synth.U14, 5),              # 640x512 14-bit
             (synth.workload_single_u8()[0].make(), synth.U8, 3),               # 320x240 u8
             (synth.make_frame(123, 201, synth.U14, 77, 8.0, 0.3), synth.U14, 9),  # ragged, unaligned rows
+            # the dense 7x7 path (sliding items), both pixel types, a ragged edge
+            (synth.make_frame(200, 330, synth.U14, 80, 8.0, 0.2), synth.U14, 7),
+            (synth.make_frame(97, 140, synth.U8, 81, 2.0, 0.2), synth.U8, 7),
             # the bit-plane strategy of the large windows, both pixel types, odd widths
             (synth.make_frame(150, 203, synth.U8, 78, 2.0, 0.2), synth.U8, 15),
             (synth.make_frame(131, 257, synth.U14, 79, 8.0, 0.2, "rv"), synth.U14, 21),
