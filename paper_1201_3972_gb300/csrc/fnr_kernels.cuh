@@ -6,13 +6,17 @@
 //   * the producer resolves each tile, waits until every consumer released
 //     the staging buffer, and stages the tile plus a k-1 pixel halo with one
 //     2-D TMA load (or clamped plain loads when the frame is not 16-byte
-//     aligned); two buffers, so the next tile loads while this one computes;
+//     aligned); two buffers (three for the dense strategies), so the next
+//     tiles load while this one computes;
 //   * each consumer warp owns a horizontal strip of tile_h/8 output rows: it
 //     replicates the frame border into the zero-filled cells it reads,
 //     computes g_min and g_max of every window (Eq. 3a/3b), flags the pixels
 //     equal to one of them (Sec. 3.3, step 2), replaces flagged pixels by the
-//     window median g_m (Sec. 3.4), writes its strip with a TMA store (or
-//     plain stores) and releases the buffer.
+//     window median g_m (Sec. 3.4) and releases the buffer. The dense
+//     strategies (k = 3, 5, 7) take every pixel's median with networks shared
+//     by neighbouring windows and store straight from registers; the
+//     compacted ones (network, bit planes) list the flagged pixels, select
+//     their medians and write the strip with a TMA store (or plain stores).
 // All arithmetic is integer min/max/compare, so results are bit-exact.
 #pragma once
 
@@ -1090,26 +1094,27 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane) {
   return x;
 }
 
-// Bit planes of the stage rows [r0, r0 + rows): word (bit b, row i, column
-// word w) at planes[(b * rows + i) * PW + w] holds bit b of the 32 pixels of
-// row r0 + i from column 32w. This order keeps the selection's reads, where
-// each lane reads its own pixel's rows at one bit, in distinct banks. Lane l
-// packs the pixels of column 32w + l of 32 / NB consecutive rows (2 of 16
-// bits, 4 of 8 bits) into one word; one warp transpose turns the 32 words
-// into the 32 plane words of those rows (lane q * NB + b: bit b of the
-// group's row q), each stored by its lane. The last word of every row is
-// zero (a window segment may reach into it). Returns the OR of the pixels.
+// Bit planes of the stage rows [r0, r0 + rows): word (bit b, row i, word w)
+// at planes[(b * rows + i) * PW + w] holds bit b of the 32 pixels of row
+// r0 + i from stage column c0 + 32w, where c0 is the first column a window of
+// the tile reads (bits beyond the stage are zero). This order keeps the
+// selection's reads, where each lane reads its own pixel's rows at one bit,
+// in distinct banks. Lane l packs the pixels of its column of 32 / NB
+// consecutive rows (2 of 16 bits, 4 of 8 bits) into one word; one warp
+// transpose turns the 32 words into the 32 plane words of those rows (lane
+// q * NB + b: bit b of the group's row q), each stored by its lane. Returns
+// the OR of the pixels.
 template <typename T>
-__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int r0, int rows, int PW, int lane) {
+__device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int c0, int r0, int rows, int PW,
+                                      int lane) {
   constexpr int NB = 8 * sizeof(T);
   constexpr int P = 32 / NB;  // rows per transpose
-  const int wpr = PW - 1;
   const int groups = (rows + P - 1) / P;
   const int b = lane & (NB - 1), q = lane / NB;  // the plane word this lane holds after a transpose
   uint32_t orv = 0;
-  for (int it = 0; it < groups * wpr; ++it) {
-    const int g = it / wpr, w = it - g * wpr;
-    const int col = (w << 5) + lane;
+  for (int it = 0; it < groups * PW; ++it) {
+    const int g = it / PW, w = it - g * PW;
+    const int col = c0 + (w << 5) + lane;
     uint32_t x = 0;
 #pragma unroll
     for (int j = 0; j < P; ++j) {
@@ -1122,7 +1127,6 @@ __device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int 
     const int row = g * P + q;
     if (row < rows) planes[(b * rows + row) * PW + w] = x;
   }
-  for (int it = lane; it < NB * rows; it += 32) planes[it * PW + wpr] = 0u;
   __syncwarp();
 #pragma unroll
   for (int j = 1; j < P; ++j) orv |= orv >> (NB * j);
@@ -1135,19 +1139,16 @@ __device__ uint32_t build_planes_warp(const T *S, uint32_t *planes, int BW, int 
 // Plane rows are relative to the strip's first stage row. Windows up to 16
 // wide keep two rows per register (segments of rows 2j and 2j+1 in the low
 // and high halves), so one popcount serves both.
-template <typename T, int K>
-__device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *list, int F, int TW, int rows, int PW,
-                               int NB, int r0, int lane) {
-  constexpr int R = (K - 1) / 2;
-  constexpr int XOFF = xoff_for(R, sizeof(T));
+template <typename T, int K, bool kTwoWords>
+__device__ __forceinline__ void bitplane_select(const uint32_t *planes, T *O, const uint16_t *list, int F, int TW,
+                                                int rows, int PW, int NB, int r0, int lane) {
   constexpr uint32_t kMask = (1u << K) - 1u;
   constexpr bool kPack = K <= 16;
   constexpr int NA = kPack ? (K + 1) / 2 : K;  // alive words
   for (int i = lane; i < F; i += 32) {
     const int e = list[i];
     const int q = e >> 8, tx = e & 255;
-    const int c0 = XOFF - R + tx;
-    const int wi = c0 >> 5, sh = c0 & 31;
+    const int wi = kTwoWords ? 0 : tx >> 5, sh = tx & 31;
     uint32_t alive[NA];
 #pragma unroll
     for (int a = 0; a < NA; ++a)
@@ -1155,17 +1156,24 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
     uint32_t rank = (K * K - 1) / 2, res = 0;
     for (int b = NB - 1; b >= 0; --b) {
       const uint32_t *P = planes + (b * rows + q) * PW + wi;
+      // the window's bits of plane row r: bits sh .. sh + K - 1 of words wi, wi + 1
+      auto row_bits = [&](int r) {
+        if constexpr (kTwoWords) {  // a row is two words: one aligned 8-byte read
+          const uint2 w = *reinterpret_cast<const uint2 *>(P + 2 * r);
+          return __funnelshift_r(w.x, w.y, sh);
+        } else {
+          return __funnelshift_r(P[r * PW], P[r * PW + 1], sh);
+        }
+      };
       uint32_t seg[NA];
       uint32_t cnt = 0;
 #pragma unroll
       for (int a = 0; a < NA; ++a) {
         if constexpr (kPack) {
           const int ra = 2 * a, rb = 2 * a + 1 < K ? 2 * a + 1 : 2 * a;
-          const uint32_t lo = __funnelshift_r(P[ra * PW], P[ra * PW + 1], sh);
-          const uint32_t hi = __funnelshift_r(P[rb * PW], P[rb * PW + 1], sh);
-          seg[a] = __byte_perm(lo, hi, 0x5410);  // bits beyond K in each half meet no live bit
+          seg[a] = __byte_perm(row_bits(ra), row_bits(rb), 0x5410);  // bits beyond K in each half meet no live bit
         } else {
-          seg[a] = __funnelshift_r(P[a * PW], P[a * PW + 1], sh);
+          seg[a] = row_bits(a);
         }
         cnt += __popc(alive[a] & ~seg[a]);
       }
@@ -1179,6 +1187,18 @@ __device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *lis
     }
     O[(r0 + q) * TW + tx] = static_cast<T>(res);
   }
+}
+
+// Flagged pixels of the strip (see bitplane_select). A tile of at most 32
+// columns keeps two plane words per row (PW == 2, set by the layout only for
+// such tiles), read as one aligned 8-byte word.
+template <typename T, int K>
+__device__ void bitplane_strip(const uint32_t *planes, T *O, const uint16_t *list, int F, int TW, int rows, int PW,
+                               int NB, int r0, int lane) {
+  if (PW == 2)
+    bitplane_select<T, K, true>(planes, O, list, F, TW, rows, PW, NB, r0, lane);
+  else
+    bitplane_select<T, K, false>(planes, O, list, F, TW, rows, PW, NB, r0, lane);
 }
 
 // Sparse strips (few flagged pixels): building the strip's bit planes costs
@@ -1589,7 +1609,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<ALGO, K>::value) fnr_kerne
           radix_sparse_strip<T, K>(S, O, list, flagged, TW, BW, r0, lane);
         } else {
           uint32_t *planes = reinterpret_cast<uint32_t *>(wbase + L.w_planes);
-          const uint32_t orv = build_planes_warp<T>(S, planes, BW, r0, L.plane_rows, L.pw, lane);
+          const uint32_t orv = build_planes_warp<T>(S, planes, BW, XOFF - R, r0, L.plane_rows, L.pw, lane);
           bitplane_strip<T, K>(planes, O, list, flagged, TW, L.plane_rows, L.pw, 32 - __clz(static_cast<int>(orv)),
                                r0, lane);
         }

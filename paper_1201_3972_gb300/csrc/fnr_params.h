@@ -177,7 +177,12 @@ __host__ __device__ inline Layout make_layout(int esize, int k, int algo, int ti
     const int need = tile_w / 2 - 4 + nwr;
     L.nps = align_up(L.np > need ? L.np : need, 4);
   }
-  L.pw = (L.bw + 31) / 32 + 1;
+  // bit-plane words per row, from stage column xoff - r (the first column a
+  // window of the tile reads): a window starting at tile column tx reads bits
+  // tx .. tx + 2r of words tx / 32 and tx / 32 + 1. Tiles up to 32 columns
+  // whose windows fit in 64 bits keep exactly two words (read as one 8-byte
+  // word); wider ones keep the words the windows reach plus one more.
+  L.pw = (tile_w <= 32 && tile_w + 2 * L.r <= 64) ? 2 : (tile_w + 2 * L.r + 31) / 32 + 1;
   L.nbmax = 8 * esize;
   L.sr = tile_h / kConsumerWarps;
   L.plane_rows = L.sr + k - 1;
