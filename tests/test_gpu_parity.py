@@ -58,7 +58,8 @@ def tiles_for(es, k, algo):
     xoff = -(-r // (16 // es)) * (16 // es)
     mult = 8 * (2 if algo in DENSE_ALGOS else row_group(k))
     out = []
-    for tw, th in ((64, 64), (128, 32), (32, 16), (16, 16), (8, 16), (128, 64), (192, 32), (64, 128), (128, 128)):
+    for tw, th in ((64, 64), (128, 32), (32, 16), (16, 16), (8, 16), (128, 64), (192, 32), (64, 128), (128, 128),
+                   (128, 48), (64, 96)):
         if tw + 2 * xoff <= 256 and th + 2 * r <= 256 and (tw * es) % 16 == 0 and th % mult == 0:
             out.append((tw, th))
     return out
