@@ -568,6 +568,16 @@ struct DenseEmit {
     } else {
       c = __byte_perm(static_cast<uint32_t>(centre[J]), static_cast<uint32_t>(centre[BW + J]), 0x5410);
     }
+    finish<J>(gm, gmin, gmax, c);
+  }
+  // the same, with the centre pixels taken from the network's input words a
+  // (row y) and b (row y + 1), x-packed with 16-bit lanes for both pixel types
+  template <int J>
+  __device__ __forceinline__ void put(uint32_t gm, uint32_t gmin, uint32_t gmax, uint32_t a, uint32_t b) {
+    finish<J>(gm, gmin, gmax, (J & 1) ? __byte_perm(a, b, 0x7632) : __byte_perm(a, b, 0x5410));
+  }
+  template <int J>
+  __device__ __forceinline__ void finish(uint32_t gm, uint32_t gmin, uint32_t gmax, uint32_t c) {
     // per 16-bit lane: 1 where the pixel is a signal pixel, 0 where noisy
     uint32_t sig;
     if constexpr (MODE == kModeMedian)

@@ -310,6 +310,7 @@ def _columns(p: Prog, k: int, w_first: int, w_end: int):
             cols[w0 + 2 * w + 1] = [p.hi(top[i], bot[i]) for i in range(k)]
         return cols[c]
 
+    col.rows = rows_of  # the input words of a word column, rows 0 .. k
     return col
 
 
@@ -348,6 +349,11 @@ def span_program(k: int):
     outs_a = horizontal(p, col, k, -n)
     ahead_a = [v for j in range(LOOKAHEAD[k]) for h in (0, 1) for v in col(w0 + 2 * (nw + j - shift) + h)]
     outs_b = horizontal(p, col, k, 0)
+    # each output also carries the x-packed words of its centre pixels (rows
+    # y and y + 1 are the item's stage rows R and R + 1): the flag test takes
+    # them from the words the network loaded, not from shared memory again
+    R = (k - 1) // 2
+    outs_b = [(o, *rest, col.rows((o - w0) // 2)[R], col.rows((o - w0) // 2)[R + 1]) for o, *rest in outs_b]
     ahead_b = [v for j in range(LOOKAHEAD[k]) for h in (0, 1) for v in col(w0 + 2 * (nw + j) + h)]
     da = _ancestors(p, [v for o in outs_a for v in o[1:]] + ahead_a)
     db = _ancestors(p, [v for o in outs_b for v in o[1:]] + ahead_b)
@@ -462,8 +468,10 @@ def _emit_ops(k: int, ops, outs, lines: List[str], indent: str = "    ", pairs: 
     for o in outs:
         done_at.setdefault(max(v for v in o[1:] if v in defined) if any(v in defined for v in o[1:]) else -1,
                            []).append(o)
+    def put(o):
+        return f"{indent}emit.template put<{o[0]}>(" + ", ".join(f"v{v}" for v in o[1:]) + ");"
     for o in sorted(done_at.pop(-1, []), key=lambda o: o[0]):
-        lines.append(f"{indent}emit.template put<{o[0]}>(v{o[1]}, v{o[2]}, v{o[3]});")
+        lines.append(put(o))
     # words (w, w + 1) of a row that start on an 8-byte boundary of the stage
     # (w of parity `par`) are read by one shared load where both are read
     par = (-first_word_col(k) // 2) % 2
@@ -498,7 +506,7 @@ def _emit_ops(k: int, ops, outs, lines: List[str], indent: str = "    ", pairs: 
         elif kind == "hi":
             lines.append(f"{indent}const uint32_t v{d} = __byte_perm(v{args[0]}, v{args[1]}, 0x7632);")
         for o in sorted(done_at.get(d, []), key=lambda o: o[0]):
-            lines.append(f"{indent}emit.template put<{o[0]}>(v{o[1]}, v{o[2]}, v{o[3]});")
+            lines.append(put(o))
 
 
 def _shape(k: int, sliding: bool) -> List[str]:
@@ -538,8 +546,9 @@ def emit_sliding(k: int) -> List[str]:
              f"  static constexpr int kCarry = {nc};",
              "  // ld.get<row, word>(): x-packed word `word` (columns x0 + kFirstCol + 2 word and the next)",
              "  // of stage row `row` of the item at x0 (0 .. k); ld.get2<row, word>(a, b): words `word` and",
-             "  // `word` + 1 by one 8-byte aligned read; emit.put<j>(g_m, g_min, g_max) gets the",
-             "  // row-packed results of output column x0 + j (low half row y, high half row y + 1)",
+             "  // `word` + 1 by one 8-byte aligned read; emit.put<j>(g_m, g_min, g_max, a, b) gets the",
+             "  // row-packed results of output column x0 + j (low half row y, high half row y + 1) and the",
+             "  // x-packed words a, b of rows y and y + 1 that hold the centre pixels of column x0 + j",
              "  // pre: the carry of the item at x0, from its first word columns",
              "  template <class Op, class Load>",
              f"  __device__ __forceinline__ static void pre(const Op op, Load &&ld, uint32_t (&c)[{nc}]) {{"]

@@ -189,7 +189,7 @@ def test_span_random_values(k):
         inputs.update(zip(carry_in, carry))
         v = gs.evaluate(body, inputs, lane_min, lane_max, lo, hi)
         carry = [v[d] for d in carry_out]
-        for o, med, gmn, gmx in outs:
+        for o, med, gmn, gmx, *centre in outs:
             c0 = it * n + o - R - w0                 # first window column in the image
             for half in (0, 1):
                 win = imgs[:, half:half + k, c0:c0 + k].reshape(trials, -1)
@@ -197,6 +197,10 @@ def test_span_random_values(k):
                 assert np.array_equal((v[med] >> (16 * half)) & mask, srt[:, (k * k - 1) // 2]), (it, o, half)
                 assert np.array_equal((v[gmn] >> (16 * half)) & mask, srt[:, 0]), (it, o, half)
                 assert np.array_equal((v[gmx] >> (16 * half)) & mask, srt[:, -1]), (it, o, half)
+            # the words handed to the flag test hold the centre pixel (column o of rows y, y + 1)
+            # in the half the emitter picks for o's parity
+            for word, row in zip(centre, (R, R + 1)):
+                assert np.array_equal((v[word] >> (16 * (o & 1))) & mask, imgs[:, row, c0 + R]), (it, o, row)
 
 
 def test_span_op_counts_recorded():
