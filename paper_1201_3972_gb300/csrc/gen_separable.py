@@ -40,10 +40,23 @@ A value that is never read is not computed (dead-code pruning); a min/max
 pair of the same operands is emitted as a compare-exchange so that part of
 the maxima can go to the FMA pipe (PackedOp::cmax).
 
+Sliding form (the 7x7, SLIDING[k]): neighbouring items of a row pair share
+sorted columns and merged blocks, so a lane filters a span of items and
+hands these on in registers. span_program() builds the program of two
+neighbouring items, takes the values of the left one that the right one
+reads as the carry (after moving transpositions whose inputs the left item
+holds to the left item when that shrinks it), pairs each carried value with
+its counterpart one item further right by structure (the same function of
+the same relative words), and returns `pre` (the carry of a span's first
+item) and `body` (one item from its carry, leaving the next item's carry).
+Each output of the sliding form also names the input words of its centre
+pixels, so the flag test needs no second read of the stage.
+
 Run this file to rewrite ``fnr_separable.cuh``; the tests import it to check
 the vertical network exhaustively, the horizontal network over every 0-1
 input with sorted columns (which by the 0-1 principle covers every input),
-the whole item on random values, and that the header is current.
+the whole item and the sliding form (pre, then bodies with the carry handed
+on) on random values, and that the header is current.
 """
 from __future__ import annotations
 
